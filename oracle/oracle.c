@@ -1,0 +1,216 @@
+/*
+ * CPU oracle for maximal all-ones square detection — TEST INFRASTRUCTURE ONLY.
+ * See oracle.h for the contract, the paper reference and the parity status.
+ * Plain single-threaded C, written for checking by eye, not for speed.
+ */
+#include "oracle.h"
+#include <stdlib.h>
+
+#define V(i, j) (v[(int64_t)(i) * ld + (j)] != 0)
+
+static void set_empty(oracle_result* out) {
+  out->side = 0;
+  out->row = -1;
+  out->col = -1;
+  out->status = 0;
+}
+
+/* Textbook DP, Sec. 1 / Eq. 1 (Sec. 2.1):
+ *   dp[i][j] = min(dp[i-1][j], dp[i][j-1], dp[i-1][j-1]) + 1  if v[i][j] = 1,
+ *   dp[i][j] = 0                                              if v[i][j] = 0,
+ * with dp = 0 outside the matrix.  K = max dp; the witness is the first (i, j)
+ * in row-major order with dp[i][j] = K. */
+int oracle_dp(const uint8_t* v, int64_t m, int64_t n, int64_t ld, int32_t* dp, int64_t ld_dp,
+              oracle_result* out) {
+  set_empty(out);
+  if (m <= 0 || n <= 0) return 0;
+  int32_t* table = dp;
+  int64_t ldt = ld_dp;
+  if (!table) {
+    table = (int32_t*)malloc((size_t)(m * n) * sizeof(int32_t));
+    if (!table) return -1;
+    ldt = n;
+  }
+  for (int64_t i = 0; i < m; ++i) {
+    for (int64_t j = 0; j < n; ++j) {
+      int32_t d = 0;
+      if (V(i, j)) {
+        int32_t up = (i > 0) ? table[(i - 1) * ldt + j] : 0;
+        int32_t left = (j > 0) ? table[i * ldt + j - 1] : 0;
+        int32_t diag = (i > 0 && j > 0) ? table[(i - 1) * ldt + j - 1] : 0;
+        int32_t mn = up < left ? up : left;
+        mn = mn < diag ? mn : diag;
+        d = mn + 1;
+      }
+      table[i * ldt + j] = d;
+    }
+  }
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j)
+      if (table[i * ldt + j] > out->side) {
+        out->side = table[i * ldt + j];
+        out->row = (int32_t)i;
+        out->col = (int32_t)j;
+      }
+  if (!dp) free(table);
+  return 0;
+}
+
+/* The same recurrence with one row of dp kept (the O(n)-space variant the
+ * paper compares against in Sec. 4.9).  prev[j] holds dp[i-1][j]. */
+int oracle_dp_rows(const uint8_t* v, int64_t m, int64_t n, int64_t ld, oracle_result* out) {
+  set_empty(out);
+  if (m <= 0 || n <= 0) return 0;
+  int32_t* prev = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+  int32_t* cur = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+  if (!prev || !cur) {
+    free(prev);
+    free(cur);
+    return -1;
+  }
+  for (int64_t i = 0; i < m; ++i) {
+    for (int64_t j = 0; j < n; ++j) {
+      int32_t d = 0;
+      if (V(i, j)) {
+        int32_t up = prev[j];
+        int32_t left = (j > 0) ? cur[j - 1] : 0;
+        int32_t diag = (j > 0) ? prev[j - 1] : 0;
+        int32_t mn = up < left ? up : left;
+        mn = mn < diag ? mn : diag;
+        d = mn + 1;
+      }
+      cur[j] = d;
+      if (d > out->side) {
+        out->side = d;
+        out->row = (int32_t)i;
+        out->col = (int32_t)j;
+      }
+    }
+    int32_t* t = prev;
+    prev = cur;
+    cur = t;
+  }
+  free(prev);
+  free(cur);
+  return 0;
+}
+
+/* Algorithm 1 (Sec. 3.2), in the paper's order and with its variables:
+ * freq[] tracks the vertical run of ones per column, counter the horizontal
+ * run of columns whose freq reaches the height threshold, and a square of side
+ * check_max_width is validated when counter reaches that width.  Both
+ * thresholds and found_max_width then grow by one and counter restarts.  The
+ * paper returns found_max_width squared (the area); this returns the side and
+ * records where each validation happened. */
+int oracle_freq(const uint8_t* v, int64_t m, int64_t n, int64_t ld, oracle_result* out) {
+  set_empty(out);
+  if (m <= 0 || n <= 0) return 0; /* empty matrix: the algorithm returns 0 */
+  const int64_t row_size = n; /* number of columns */
+  const int64_t col_size = m; /* number of rows */
+  int64_t found_max_width = 0;
+  int64_t check_max_width = 1;
+  int64_t check_max_height = 1;
+  int64_t counter = 0;
+  int64_t* freq = (int64_t*)calloc((size_t)row_size, sizeof(int64_t));
+  if (!freq) return -1;
+  for (int64_t i = 0; i < col_size; ++i) {
+    counter = 0;
+    for (int64_t j = 0; j < row_size; ++j) {
+      if (!V(i, j)) {
+        freq[j] = 0;
+        counter = 0;
+        continue;
+      }
+      freq[j] = freq[j] + 1;
+      if (freq[j] < check_max_height) {
+        counter = 0;
+        continue;
+      }
+      counter = counter + 1;
+      if (counter == check_max_width) {
+        found_max_width = found_max_width + 1;
+        check_max_width = check_max_width + 1;
+        check_max_height = check_max_height + 1;
+        counter = 0;
+        out->row = (int32_t)i; /* record of this validation */
+        out->col = (int32_t)j;
+      }
+    }
+  }
+  free(freq);
+  out->side = (int32_t)found_max_width;
+  return 0;
+}
+
+/* DP map from the frequency array.  After row i, freq[j] is the vertical run of
+ * ones ending at (i, j) (the frequency invariant of Sec. 3.4).  A k x k square
+ * with bottom-right corner (i, j) is all ones exactly when the k columns
+ * j-k+1..j each have a run of at least k, so
+ *   dp[i][j] = max{k >= 0 : j-k+1 >= 0 and min(freq[j-k+1..j]) >= k},
+ * found here by trying k = 1, 2, ... while the running minimum allows it. */
+int oracle_freq_dpmap(const uint8_t* v, int64_t m, int64_t n, int64_t ld, int32_t* dp,
+                      int64_t ld_dp, oracle_result* out) {
+  set_empty(out);
+  if (m <= 0 || n <= 0) return 0;
+  int64_t* freq = (int64_t*)calloc((size_t)n, sizeof(int64_t));
+  if (!freq) return -1;
+  for (int64_t i = 0; i < m; ++i) {
+    for (int64_t j = 0; j < n; ++j) freq[j] = V(i, j) ? freq[j] + 1 : 0;
+    for (int64_t j = 0; j < n; ++j) {
+      int64_t k = 0;
+      int64_t run_min = INT64_MAX;
+      while (j - k >= 0) {
+        int64_t f = freq[j - k];
+        run_min = f < run_min ? f : run_min;
+        if (run_min < k + 1) break;
+        ++k;
+      }
+      if (dp) dp[i * ld_dp + j] = (int32_t)k;
+      if (k > out->side) {
+        out->side = (int32_t)k;
+        out->row = (int32_t)i;
+        out->col = (int32_t)j;
+      }
+    }
+  }
+  free(freq);
+  return 0;
+}
+
+static int square_all_ones(const uint8_t* v, int64_t ld, int64_t r, int64_t c, int64_t s) {
+  for (int64_t i = r; i < r + s; ++i)
+    for (int64_t j = c; j < c + s; ++j)
+      if (!V(i, j)) return 0;
+  return 1;
+}
+
+/* Brute force over every square: for each side s from the largest possible
+ * down, scan the bottom-right corners in row-major order and return the first
+ * all-ones one. */
+int oracle_brute(const uint8_t* v, int64_t m, int64_t n, int64_t ld, oracle_result* out) {
+  set_empty(out);
+  if (m <= 0 || n <= 0) return 0;
+  int64_t smax = m < n ? m : n;
+  for (int64_t s = smax; s >= 1; --s)
+    for (int64_t i = s - 1; i < m; ++i)
+      for (int64_t j = s - 1; j < n; ++j)
+        if (square_all_ones(v, ld, i - s + 1, j - s + 1, s)) {
+          out->side = (int32_t)s;
+          out->row = (int32_t)i;
+          out->col = (int32_t)j;
+          return 0;
+        }
+  return 0;
+}
+
+int oracle_erode(const uint8_t* v, int64_t m, int64_t n, int64_t ld, int64_t t, uint8_t* s,
+                 int64_t ld_s) {
+  if (t < 1) return -1;
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      int ok = (i - t + 1 >= 0) && (j - t + 1 >= 0);
+      if (ok) ok = square_all_ones(v, ld, i - t + 1, j - t + 1, t);
+      s[i * ld_s + j] = (uint8_t)ok;
+    }
+  return 0;
+}
