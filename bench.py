@@ -1,0 +1,565 @@
+"""Benchmark: maximal all-ones square detection on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  A step is one pass of the hot path over the
+workload's matrices: the tile pass, the exact fix-up when needed and the
+result write-out, for every matrix.  Inputs are generated in HBM by the
+seeded generator before timing; `value` is cells/s over K device-timed steps
+(max over ranks); `e2e` repeats the measurement with the inputs in pinned
+host memory and the host->device copies and the result read-back inside the
+timed region.  `--impl reference` times the CPU oracle (the paper's
+Algorithm 1, single thread) on the same workload instead.
+
+Workloads (sizes from the configurations this benchmark mirrors):
+  sweep    (default) square uint8 matrices, sides 1000..5000 x densities
+           0.1..0.9 (45 matrices, 495 M cells), one call per matrix; side+witness
+  c1       256 x 256, p = 0.5, seed 0, side + witness + int32 dp map
+  c3-u8 / c3-u8-dp / c3-bits / c3-bits-dp
+           32768 x 32768, p = 0.9, one planted 600-square, seed 3
+  c4       4096 uint8 matrices, m and n log-uniform in [16, 2048], one ms_batch
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gcells/s on 1 GB300 (% HBM roofline), batched vs plain; serve p50/p99 ms"
+
+
+# ----------------------------------------------------------------- workloads --
+
+def sweep_specs():
+    specs = []
+    for side in (1000, 2000, 3000, 4000, 5000):
+        for k in range(1, 10):
+            p = k / 10
+            specs.append(dict(m=side, n=side, p=p, seed=10 * (side // 1000) + k, plant=0))
+    return specs
+
+
+def c3_spec():
+    return dict(m=32768, n=32768, p=0.9, seed=3, plant=600)
+
+
+def c4_specs(count=4096):
+    import gen
+    specs = []
+    lo, hi = math.log(16), math.log(2049)
+    for k in range(count):
+        seed = gen.draw(4, k)
+        u = lambda j: (gen.draw(seed, (1 << 40) + j) >> 11) / float(1 << 53)
+        m = min(2048, int(math.exp(lo + (hi - lo) * u(0))))
+        n = min(2048, int(math.exp(lo + (hi - lo) * u(1))))
+        p = (1 + int(9 * u(2))) / 10
+        plant = 0
+        if u(3) < 0.5:
+            plant = 1 + int(min(m, n) * u(4))
+        specs.append(dict(m=m, n=n, p=p, seed=seed, plant=plant))
+    return specs
+
+
+def round_up(x, a):
+    return (x + a - 1) // a * a
+
+
+class Mat:
+    """One generated matrix resident in HBM (and optionally in pinned host memory)."""
+
+    def __init__(self, spec, fmt, device, want_host=False):
+        import torch
+
+        import gen
+        self.spec = spec
+        self.fmt = fmt
+        m, n = spec["m"], spec["n"]
+        self.m, self.n = m, n
+        if fmt == 0:
+            self.ld = round_up(n, 16)
+            self.dev = torch.empty((m, self.ld), dtype=torch.uint8, device=device)
+            gen.fill_u8_dev(self.dev.data_ptr(), m, n, self.ld, spec["p"], spec["seed"])
+            if spec["plant"]:
+                r, c = gen.plant_pos(spec["seed"], m, n, spec["plant"])
+                gen.plant_u8_dev(self.dev.data_ptr(), self.ld, r, c, spec["plant"])
+        else:
+            self.ld = round_up((n + 31) // 32, 4)
+            self.dev = torch.empty((m, self.ld), dtype=torch.int32, device=device)
+            gen.fill_bits_dev(self.dev.data_ptr(), m, n, self.ld, spec["p"], spec["seed"])
+            if spec["plant"]:
+                r, c = gen.plant_pos(spec["seed"], m, n, spec["plant"])
+                gen.plant_bits_dev(self.dev.data_ptr(), self.ld, r, c, spec["plant"])
+        self.host = None
+        if want_host:
+            torch.cuda.synchronize()
+            self.host = torch.empty(self.dev.shape, dtype=self.dev.dtype, pin_memory=True)
+            self.host.copy_(self.dev)
+        self.view = self.dev[:, :n] if fmt == 0 else self.dev
+
+    @property
+    def nbytes(self):
+        return self.dev.numel() * self.dev.element_size()
+
+    def args(self, tensor=None):
+        t = self.dev if tensor is None else tensor
+        return (t[:, :self.n], None, 0) if self.fmt == 0 else (t, self.n, 1)
+
+
+class Workload:
+    name = ""
+    dtype = "u8"
+    bytes_per_cell = 1.0  # algorithmic bytes of the dominant kernel
+
+    def __init__(self, device):
+        self.device = device
+
+    def config(self):
+        raise NotImplementedError
+
+
+class PlainSet(Workload):
+    """A list of matrices, one plain ms_max_square / ms_dp_map call each."""
+
+    def __init__(self, device, specs, fmt=0, dpmap=False, label="", host=False):
+        super().__init__(device)
+        import torch
+        self.specs = specs
+        self.fmt = fmt
+        self.dpmap = dpmap
+        self.label = label
+        self.mats = [Mat(s, fmt, device, want_host=host) for s in specs]
+        self.cells = sum(s["m"] * s["n"] for s in specs)
+        self.res = torch.empty((len(specs), 4), dtype=torch.int32, device=device)
+        self.dps = None
+        if dpmap:
+            self.dps = [torch.empty((s["m"], s["n"]), dtype=torch.int32, device=device)
+                        for s in specs]
+        self.dtype = "u8" if fmt == 0 else "bits32"
+        self.bytes_per_cell = (1.0 if fmt == 0 else 0.125) + (4.0 if dpmap else 0.0)
+        self.dev_bufs = None
+
+    def step(self, ctx, stream=None, tensors=None):
+        for i, mt in enumerate(self.mats):
+            x, n, fmt = mt.args(None if tensors is None else tensors[i])
+            if self.dpmap:
+                ctx.dp_map(x, n=n, fmt=fmt, dp=self.dps[i], out=self.res[i], stream=stream)
+            else:
+                ctx.max_square(x, n=n, fmt=fmt, out=self.res[i], stream=stream)
+
+    def batch_step(self, ctx, stream=None):
+        ctx.batch([mt.args()[:2] if mt.fmt else mt.args()[0] for mt in self.mats],
+                  out=self.res, stream=stream)
+
+    def h2d_bytes(self):
+        return sum(mt.nbytes for mt in self.mats)
+
+    def config(self):
+        return {"workload": self.label, "matrices": len(self.specs), "cells": self.cells,
+                "format": self.dtype, "dp_map": self.dpmap,
+                "row_stride": "columns rounded up to 16 bytes" if self.fmt == 0 else
+                              "words rounded up to 4",
+                "l2": ("inputs larger than L2 (129 MB)" if self.cells * self.bytes_per_cell
+                       > 129e6 else "L2 flushed between steps")}
+
+
+def make_workload(name, device, host=False):
+    if name == "sweep":
+        return PlainSet(device, sweep_specs(), label="paper-scale sweep: square uint8, sides "
+                        "1000..5000 x p 0.1..0.9, seed 10*side/1000+10p, side + witness, "
+                        "one call per matrix", host=host)
+    if name == "c1":
+        return PlainSet(device, [dict(m=256, n=256, p=0.5, seed=0, plant=0)], dpmap=True,
+                        label="256x256 uint8, p=0.5, seed 0, side + witness + int32 dp map",
+                        host=host)
+    if name.startswith("c3"):
+        fmt = 1 if "bits" in name else 0
+        dp = name.endswith("-dp")
+        return PlainSet(device, [c3_spec()], fmt=fmt, dpmap=dp,
+                        label=f"32768x32768 {'bit-packed' if fmt else 'uint8'}, p=0.9, planted "
+                              f"600-square, seed 3, {'dp map' if dp else 'side + witness'}",
+                        host=host)
+    if name == "c4":
+        return PlainSet(device, c4_specs(), label="batch of 4096 uint8 matrices, m,n "
+                        "log-uniform in [16,2048], p in 0.1..0.9, half planted", host=host)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ------------------------------------------------------------------- helpers --
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples (200 ms) around the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def mark(self, t0, t1):
+        self.t0, self.t1 = t0, t1
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=2)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        lo, hi = (self.t0 or 0) - 0.25, (self.t1 or 1e30) + 0.25
+        rows = [s for (t, s) in self.samples if lo <= t <= hi] or [s for (_, s) in self.samples]
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                pass
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        mhz.sort()
+        return {"sm_mhz": mhz[len(mhz) // 2] if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "window": "timed region +-0.25 s, 200 ms sampling"}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_key):
+    """Per-cell DRAM traffic of a kernel from its committed ncu summary, if the
+    kernel sources are unchanged since the capture (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_summary.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"sources_sha1:\s*([0-9a-f]{40})", text)
+    h = hashlib.sha1()
+    for f in ("ms.cu", "ms_kernels.cuh", "ms_device.cuh", "ms_bits.cuh"):
+        p = os.path.join(ROOT, "paper_2503_18974_gb300", "csrc", f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    if not m or m.group(1) != h.hexdigest():
+        return None
+    m2 = re.search(rf"traffic_bytes_per_cell\[{re.escape(kernel_key)}\]:\s*([0-9.]+)", text)
+    return float(m2.group(1)) if m2 else None
+
+
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x, device):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ CPU (oracle) ----
+
+def cpu_oracle_run(specs, budget_s=20.0, reps=5):
+    """The paper's Algorithm 1 (oracle.freq, one thread) on the workload's
+    matrices regenerated on the host; the paper's protocol scaled down: one
+    warm-up, then repetitions until the budget, 10% trimmed mean."""
+    import numpy as np
+
+    import gen
+    import oracle
+    oracle.build()
+    mats = []
+    tot = 0
+    for s in specs:
+        a = gen.bernoulli_u8(s["m"], s["n"], s["p"], s["seed"])
+        if s["plant"]:
+            r, c = gen.plant_pos(s["seed"], s["m"], s["n"], s["plant"])
+            a[r:r + s["plant"], c:c + s["plant"]] = 1
+        mats.append(a)
+        tot += s["m"] * s["n"]
+    for a in mats:
+        oracle.freq(a)
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < reps and (time.perf_counter() - t_start) < budget_s:
+        t0 = time.perf_counter()
+        for a in mats:
+            oracle.freq(a)
+        times.append(time.perf_counter() - t0)
+    times.sort()
+    trim = int(len(times) * 0.1)
+    kept = times[trim:len(times) - trim] if len(times) > 2 * trim else times
+    sec = sum(kept) / len(kept)
+    t0 = time.perf_counter()
+    oracle.dp_rows(mats[len(mats) // 2])
+    dp_rate = mats[len(mats) // 2].size / (time.perf_counter() - t0)
+    return tot, sec, len(times), dp_rate
+
+
+def cpu_sample_specs(specs, max_cells=600_000_000):
+    out, tot = [], 0
+    for s in specs:
+        c = s["m"] * s["n"]
+        if tot + c > max_cells and out:
+            continue
+        out.append(s)
+        tot += c
+    return out
+
+
+def cpu_baseline(specs):
+    sample = cpu_sample_specs(specs)
+    cells, sec, reps, dp_rate = cpu_oracle_run(sample)
+    return {"value": cells / sec / 1e9, "unit": "Gcells/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(sample)} of {len(specs)} matrices ({cells / 1e6:.0f} M cells), "
+                      f"Algorithm 1 (oracle_freq), 1 warm-up + {reps} timed passes, "
+                      f"10% trimmed mean",
+            "oracle_dp_rows_gcells_s": dp_rate / 1e9}
+
+
+# ------------------------------------------------------------------- arms -----
+
+def run_reference(args, world, rank, local, pg):
+    if rank != 0:
+        return
+    specs = {"sweep": sweep_specs, "c1": lambda: [dict(m=256, n=256, p=0.5, seed=0, plant=0)],
+             "c4": c4_specs}.get(args.workload, lambda: [c3_spec()])()
+    sample = cpu_sample_specs(specs, max_cells=120_000_000)
+    import gen
+    import oracle
+    oracle.build()
+    mats = []
+    for s in sample:
+        a = gen.bernoulli_u8(s["m"], s["n"], s["p"], s["seed"])
+        if s["plant"]:
+            r, c = gen.plant_pos(s["seed"], s["m"], s["n"], s["plant"])
+            a[r:r + s["plant"], c:c + s["plant"]] = 1
+        mats.append(a)
+    cells = sum(a.size for a in mats)
+    for _ in range(args.warmup):
+        for a in mats:
+            oracle.freq(a)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for a in mats:
+            oracle.freq(a)
+    dt = time.perf_counter() - t0
+    value = cells * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gcells/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": args.workload, "sample_matrices": len(mats),
+                       "sample_cells": cells},
+            "cpu_baseline": {"value": value, "unit": "Gcells/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: {len(mats)} of {len(specs)} matrices "
+                                       f"({cells / 1e6:.0f} M cells) through Algorithm 1"},
+            "e2e": {"value": value, "unit": "Gcells/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+
+    import paper_2503_18974_gb300 as ms
+    device = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(device)
+    ms.build()
+    ctx = ms.MaxSquare(local)
+    wl = make_workload(args.workload, device, host=True)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+
+    # warm-up (also sizes the workspace)
+    for _ in range(args.warmup):
+        wl.step(ctx)
+    torch.cuda.synchronize()
+
+    # timed region: K steps, device-timed
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    barrier(pg)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        wl.step(ctx)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier(pg)
+    sampler.mark(t_wall0, t_wall1)
+    clocks = sampler.stop()
+    ms_total = max_over_ranks(pg, ev0.elapsed_time(ev1), device)
+    ms_step = ms_total / args.steps
+    value = world * wl.cells * args.steps / (ms_total * 1e-3) / 1e9
+
+    # dominant kernel (tile pass): the same K steps again with a CUDA event pair
+    # recorded by the library around every launch on this stream; achieved =
+    # algorithmic bytes / summed tile-kernel time
+    ctx.profile_start()
+    for _ in range(args.steps):
+        wl.step(ctx)
+    prof = ctx.profile_stop()
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if prof.tile_launches and prof.tile_ms > 0:
+        alg_bytes = wl.cells * wl.bytes_per_cell * args.steps
+        achieved = alg_bytes / (prof.tile_ms * 1e-3) / 1e9
+        traffic = profile_traffic(args.workload)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak,
+                "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs)"
+                                if peak_kind == "measured" else "of fallback 6800 GB/s"),
+                "traffic": (traffic * wl.cells if traffic is not None else None),
+                "kernel": "k_tiles_one (tile pass)", "bytes_per_cell": wl.bytes_per_cell,
+                "launches_per_step": prof.tile_launches / args.steps,
+                "tile_ms_per_step": prof.tile_ms / args.steps,
+                "fixup_ms_per_step": prof.fixup_ms / args.steps,
+                "how": "per-launch CUDA events on the launching stream, same K steps re-run"}
+    launches = (prof.tile_launches + prof.fixup_launches + prof.other_launches)
+
+    # batched form of the same workload (one ms_batch per step)
+    batched = None
+    if len(wl.mats) > 1 and not wl.dpmap:
+        for _ in range(2):
+            wl.batch_step(ctx)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            wl.batch_step(ctx)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        bms = ev0.elapsed_time(ev1) / args.steps
+        batched = {"value": wl.cells / (bms * 1e-3) / 1e9, "unit": "Gcells/s", "ms_per_step": bms,
+                   "how": "one ms_batch call per step over the same matrices"}
+
+    # e2e: inputs in pinned host memory, copies and result read-back timed
+    bufs = [torch.empty_like(mt.dev) for mt in wl.mats]
+    res_host = torch.empty(wl.res.shape, dtype=torch.int32, pin_memory=True)
+    for _ in range(max(1, args.warmup)):
+        for b, mt in zip(bufs, wl.mats):
+            b.copy_(mt.host, non_blocking=True)
+        wl.step(ctx, tensors=bufs)
+        res_host.copy_(wl.res, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        for b, mt in zip(bufs, wl.mats):
+            b.copy_(mt.host, non_blocking=True)
+        wl.step(ctx, tensors=bufs)
+        res_host.copy_(wl.res, non_blocking=True)
+        torch.cuda.synchronize()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(pg, (time.perf_counter() - t0) * 1e3, device)
+    e2e = {"value": world * wl.cells * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "Gcells/s",
+           "h2d_bytes_per_step": wl.h2d_bytes(), "d2h_bytes_per_step": res_host.numel() * 4,
+           "how": "pinned host inputs copied H2D, ms_* call, results read back, per step"}
+
+    # correctness spot check of the timed results against nothing stored:
+    # statuses must be MS_OK
+    ok = bool((wl.res[:, 3] == 0).all().item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(wl.specs)
+
+    if rank == 0:
+        pk = None
+        line = {"metric": METRIC, "value": value, "unit": "Gcells/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": pk,
+                "dtype": wl.dtype, "data": "synthetic (seeded SplitMix64 Bernoulli matrices)",
+                "config": {**wl.config(), "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks, "batched": batched,
+                "status_ok": ok}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world, rank, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank, local, pg)
+        else:
+            run_ours(args, world, rank, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,152 @@
+/*
+ * libms — maximal all-ones square detection on one GB300 (sm_103a).
+ *
+ * Problem (S. Bhandari, "An Efficient Frequency-Based Approach for Maximal
+ * Square Detection in Binary Matrices", arXiv 2503.18974, Sec. 1): given an
+ * m x n 0/1 matrix, find the largest k such that some k x k submatrix is all
+ * ones.  The paper's Algorithm 1 (Sec. 3.2) returns the area k*k; this
+ * library returns the side k and a deterministic witness: the bottom-right
+ * corner (row, col) of the first k-square in row-major order of that corner,
+ * which is where Algorithm 1 makes its last validation.  Optionally it writes
+ * the map dp[i][j] = side of the largest all-ones square whose bottom-right
+ * corner is (i, j) (the table of Eq. 1, Sec. 2.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - All matrix, result and dp pointers are DEVICE pointers owned by the
+ *   caller (for example torch tensors).  The library never frees them.
+ * - Every call is asynchronous on the given stream; results are valid once
+ *   that stream has been synchronised.  The library performs no host
+ *   synchronisation on the hot path.
+ * - Host-detectable problems (null pointers, negative sizes, ld < row width,
+ *   unsupported format or size) return an error immediately and launch
+ *   nothing.  Problems found on the device (a bounded wait that gave up) are
+ *   reported in ms_result.status of the affected matrix; the context stays
+ *   usable.
+ * - An empty matrix (m == 0 or n == 0) yields side 0 and row = col = -1, as
+ *   Algorithm 1 returns 0 for an empty input (Sec. 3.2).
+ * - No C++ exception crosses this interface.  A context is not thread-safe:
+ *   use one per host thread (contexts may share a device).
+ * - Size limits: m <= 65000 rows and min(m, n) <= 32768; larger inputs
+ *   return MS_ERR_UNSUPPORTED.  n itself is limited only by m*n < 2^40.
+ */
+#ifndef MS_H
+#define MS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ms_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+typedef struct ms_ctx ms_ctx;
+
+typedef enum {
+  MS_OK = 0,
+  MS_ERR_INVALID = 1,     /* bad argument */
+  MS_ERR_OOM = 2,         /* device allocation failed or workspace budget too small */
+  MS_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+  MS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (reported per matrix) */
+  MS_ERR_BUDGET = 5,      /* request does not fit the serving memory budget */
+  MS_ERR_UNSUPPORTED = 6  /* valid but outside the supported sizes or layouts */
+} ms_status;
+
+typedef enum {
+  MS_U8 = 0,    /* one byte per cell, row-major, ld = row stride in bytes (ld >= n);
+                   any nonzero byte is a one */
+  MS_BITS32 = 1 /* 32 cells per uint32 word, row-major, ld = row stride in words
+                   (ld >= ceil(n/32)); bit b (LSB = 0) of word w is column 32*w+b;
+                   bits for columns >= n are ignored */
+} ms_format;
+
+typedef struct {
+  const void* data; /* device pointer to cell (0,0) */
+  int64_t m, n;     /* rows, columns (>= 0) */
+  int64_t ld;       /* row stride in elements of the format (bytes or words) */
+  int32_t fmt;      /* ms_format */
+  int32_t reserved; /* must be 0 */
+} ms_matrix;
+
+typedef struct {
+  int32_t side;   /* largest all-ones square side, 0 if none */
+  int32_t row;    /* bottom-right corner of the first side-k square, row-major; -1 if side == 0 */
+  int32_t col;
+  int32_t status; /* MS_OK, or MS_ERR_TIMEOUT if a device-side wait gave up */
+} ms_result;
+
+/* Create a context on `device`.  workspace_budget_bytes caps the device
+ * workspace the context may hold (0 = no cap).  The workspace (job table,
+ * per-matrix witness keys, fix-up carries) grows on demand up to the cap and
+ * is owned by the context.  Returns MS_ERR_OOM if the initial workspace
+ * cannot be allocated. */
+ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes);
+
+/* Largest square side and witness of one matrix (Sec. 3.2, Algorithm 1's
+ * result as a side, with the witness described above).  `out_dev` is one
+ * ms_result in device memory. */
+ms_status ms_max_square(ms_ctx* ctx, const ms_matrix* in, ms_result* out_dev, ms_stream_t s);
+
+/* As ms_max_square, and also writes dp[i*ld_dp + j] (int32, device memory,
+ * ld_dp >= n) for every cell: the side of the largest all-ones square with
+ * bottom-right corner (i, j) (Eq. 1, Sec. 2.1).  Works for MS_U8 and
+ * MS_BITS32 input. */
+ms_status ms_dp_map(ms_ctx* ctx, const ms_matrix* in, int32_t* dp_dev, int64_t ld_dp,
+                    ms_result* out_dev, ms_stream_t s);
+
+/* Side and witness for `count` matrices of possibly different shapes and
+ * formats in one pass: the descriptors are read from HOST memory (ins_host),
+ * the results go to outs_dev[0..count-1] in device memory.  Work from all
+ * matrices is scheduled together.  After a first call with a given set of
+ * shapes, the same call (same pointers, shapes and count) may be captured in
+ * a CUDA graph: it then allocates nothing and performs no host-device copy
+ * other than stream-ordered ones issued inside the call. */
+ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_result* outs_dev,
+                   ms_stream_t s);
+
+/* Free the context and its workspace (after synchronising its device work). */
+ms_status ms_destroy(ms_ctx* ctx);
+
+/* Static, human-readable name of a status code. */
+const char* ms_status_string(ms_status st);
+
+/* ---- tuning -------------------------------------------------------------
+ * Launch parameters: `band_rows` = rows of a matrix that one tile counts
+ * (each tile also re-reads a halo of 32 rows above and 32 columns to its
+ * left), `packed_path` selects, for MS_BITS32 size-only work, the bitplane
+ * erosion search (1) or the byte-style tile kernel on unpacked bits (0).
+ * 0 for band_rows = choose automatically from the matrix size. */
+typedef struct {
+  int32_t band_rows;
+  int32_t packed_path;
+  int32_t reserved[6];
+} ms_tuning;
+
+ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t);
+ms_status ms_get_tuning(ms_ctx* ctx, ms_tuning* t);
+
+/* ---- kernel timing --------------------------------------------------------
+ * Between ms_profile_start and ms_profile_stop the context records a CUDA
+ * event pair around every kernel it launches (on the caller's stream, so the
+ * events time exactly those launches).  ms_profile_stop synchronises the
+ * recorded events and returns per-kind launch counts and summed durations.
+ * At most max_launches launches are timed; later ones run untimed and are
+ * only counted.  The events add no device work. */
+typedef struct {
+  int64_t tile_launches;   /* tile-pass kernels (the bandwidth-bound hot kernel) */
+  double tile_ms;
+  int64_t fixup_launches;  /* exact fix-up / result kernels */
+  double fixup_ms;
+  int64_t other_launches;  /* packed-search kernels and helpers */
+  double other_ms;
+  int64_t untimed_launches;
+} ms_profile;
+
+ms_status ms_profile_start(ms_ctx* ctx, int32_t max_launches);
+ms_status ms_profile_stop(ms_ctx* ctx, ms_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MS_H */

@@ -1,0 +1,228 @@
+"""Maximal all-ones square detection on GB300: Python binding of libms.
+
+Argument marshalling only.  Every step of the computation runs in the CUDA
+kernels of ``libms.so`` (built from ``csrc/``); PyTorch supplies device
+memory and streams.  There is no CPU fallback: if the library is missing or
+was built for another machine, importing the binding raises.
+
+Results are int32 device tensors ``[side, row, col, status]``: the largest
+all-ones square side, the bottom-right corner of the first such square in
+row-major order (-1, -1 when side == 0) and an ``ms_status`` code.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Iterable, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+LIB_PATH = os.path.join(_HERE, "libms.so")
+_SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_kernels.cuh", "ms_device.cuh",
+                                                      "ms_bits.cuh")]
+_HEADER = os.path.join(_ROOT, "include", "ms.h")
+
+MS_U8 = 0
+MS_BITS32 = 1
+STATUS = {0: "MS_OK", 1: "MS_ERR_INVALID", 2: "MS_ERR_OOM", 3: "MS_ERR_CUDA",
+          4: "MS_ERR_TIMEOUT", 5: "MS_ERR_BUDGET", 6: "MS_ERR_UNSUPPORTED"}
+
+NVCC_FLAGS = ["-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+              "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo"]
+
+
+class MSError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libms.so in-tree for sm_103a (nvcc cross-compiles without a GPU)."""
+    srcs = [p for p in _SOURCES + [_HEADER] if os.path.exists(p)]
+    stale = force or not os.path.exists(LIB_PATH) or any(
+        os.path.getmtime(p) > os.path.getmtime(LIB_PATH) for p in srcs)
+    if stale:
+        cmd = ["nvcc", *NVCC_FLAGS, "-o", LIB_PATH, os.path.join(_HERE, "csrc", "ms.cu")]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        subprocess.check_call(cmd)
+    return LIB_PATH
+
+
+class _Matrix(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("fmt", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("band_rows", ctypes.c_int32), ("packed_path", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("tile_launches", ctypes.c_int64), ("tile_ms", ctypes.c_double),
+                ("fixup_launches", ctypes.c_int64), ("fixup_ms", ctypes.c_double),
+                ("other_launches", ctypes.c_int64), ("other_ms", ctypes.c_double),
+                ("untimed_launches", ctypes.c_int64)]
+
+
+_lib = None
+
+EXPORTS = ("ms_create", "ms_destroy", "ms_max_square", "ms_dp_map", "ms_batch",
+           "ms_status_string", "ms_set_tuning", "ms_get_tuning", "ms_profile_start",
+           "ms_profile_stop")
+
+
+def lib():
+    """Load libms.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libms.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64 = ctypes.c_void_p, ctypes.c_int64
+        L.ms_create.restype = ctypes.c_int
+        L.ms_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_size_t]
+        L.ms_destroy.restype = ctypes.c_int
+        L.ms_destroy.argtypes = [vp]
+        L.ms_max_square.restype = ctypes.c_int
+        L.ms_max_square.argtypes = [vp, ctypes.POINTER(_Matrix), vp, vp]
+        L.ms_dp_map.restype = ctypes.c_int
+        L.ms_dp_map.argtypes = [vp, ctypes.POINTER(_Matrix), vp, i64, vp, vp]
+        L.ms_batch.restype = ctypes.c_int
+        L.ms_batch.argtypes = [vp, ctypes.POINTER(_Matrix), ctypes.c_int32, vp, vp]
+        L.ms_status_string.restype = ctypes.c_char_p
+        L.ms_status_string.argtypes = [ctypes.c_int]
+        L.ms_set_tuning.restype = ctypes.c_int
+        L.ms_set_tuning.argtypes = [vp, ctypes.POINTER(_Tuning)]
+        L.ms_get_tuning.restype = ctypes.c_int
+        L.ms_get_tuning.argtypes = [vp, ctypes.POINTER(_Tuning)]
+        L.ms_profile_start.restype = ctypes.c_int
+        L.ms_profile_start.argtypes = [vp, ctypes.c_int32]
+        L.ms_profile_stop.restype = ctypes.c_int
+        L.ms_profile_stop.argtypes = [vp, ctypes.POINTER(Profile)]
+        _lib = L
+    return _lib
+
+
+def _check(code: int, what: str) -> None:
+    if code != 0:
+        raise MSError(code, what)
+
+
+def describe(x, n: int | None = None, fmt: int | None = None) -> _Matrix:
+    """ms_matrix for a 2-D CUDA tensor: uint8 cells (MS_U8) or 32-bit words of
+    packed bits (MS_BITS32, n = number of columns required)."""
+    import torch
+    if x.dim() != 2 or x.stride(1) != 1:
+        raise ValueError("expected a 2-D tensor with unit column stride")
+    if fmt is None:
+        fmt = MS_U8 if x.dtype == torch.uint8 else MS_BITS32
+    if fmt == MS_U8:
+        if x.dtype != torch.uint8:
+            raise ValueError("MS_U8 expects a uint8 tensor")
+        n = x.shape[1] if n is None else n
+    else:
+        if x.dtype not in (torch.int32, torch.uint32):
+            raise ValueError("MS_BITS32 expects an int32/uint32 tensor of packed words")
+        if n is None:
+            raise ValueError("MS_BITS32 needs the column count n")
+    ld = x.stride(0) if x.shape[0] > 1 else max(x.shape[1], 1)
+    return _Matrix(x.data_ptr(), x.shape[0], n, ld, fmt, 0)
+
+
+def _stream_ptr(stream) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream or None
+
+
+class MaxSquare:
+    """A libms context on one device."""
+
+    def __init__(self, device: int = 0, workspace_budget: int = 0):
+        self.device = device
+        h = ctypes.c_void_p()
+        _check(lib().ms_create(ctypes.byref(h), device, workspace_budget), "ms_create")
+        self._h = h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().ms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tuning(self, band_rows: int = 0, packed_path: int = 0) -> None:
+        t = _Tuning(band_rows, packed_path)
+        _check(lib().ms_set_tuning(self._h, ctypes.byref(t)), "ms_set_tuning")
+
+    def profile_start(self, max_launches: int = 1 << 20) -> None:
+        _check(lib().ms_profile_start(self._h, max_launches), "ms_profile_start")
+
+    def profile_stop(self) -> Profile:
+        p = Profile()
+        _check(lib().ms_profile_stop(self._h, ctypes.byref(p)), "ms_profile_stop")
+        return p
+
+    def get_tuning(self) -> dict:
+        t = _Tuning()
+        _check(lib().ms_get_tuning(self._h, ctypes.byref(t)), "ms_get_tuning")
+        return {"band_rows": t.band_rows, "packed_path": t.packed_path}
+
+    def max_square(self, x, n: int | None = None, fmt: int | None = None, out=None, stream=None):
+        import torch
+        desc = describe(x, n, fmt)
+        if out is None:
+            out = torch.empty(4, dtype=torch.int32, device=x.device)
+        _check(lib().ms_max_square(self._h, ctypes.byref(desc), out.data_ptr(),
+                                   _stream_ptr(stream)), "ms_max_square")
+        return out
+
+    def dp_map(self, x, n: int | None = None, fmt: int | None = None, dp=None, out=None,
+               stream=None):
+        import torch
+        desc = describe(x, n, fmt)
+        if dp is None:
+            dp = torch.empty((desc.m, desc.n), dtype=torch.int32, device=x.device)
+        if out is None:
+            out = torch.empty(4, dtype=torch.int32, device=x.device)
+        ld_dp = dp.stride(0) if dp.dim() == 2 and dp.shape[0] > 1 else max(desc.n, 1)
+        _check(lib().ms_dp_map(self._h, ctypes.byref(desc), dp.data_ptr(), ld_dp, out.data_ptr(),
+                               _stream_ptr(stream)), "ms_dp_map")
+        return dp, out
+
+    def batch(self, mats: Sequence, out=None, stream=None):
+        """mats: tensors (uint8) or (tensor, n) / (tensor, n, fmt) tuples."""
+        import torch
+        descs = (_Matrix * max(len(mats), 1))()
+        dev = None
+        for i, item in enumerate(mats):
+            if isinstance(item, tuple):
+                descs[i] = describe(*item)
+                dev = item[0].device
+            else:
+                descs[i] = describe(item)
+                dev = item.device
+        if out is None:
+            out = torch.empty((len(mats), 4), dtype=torch.int32,
+                              device=dev if dev is not None else f"cuda:{self.device}")
+        _check(lib().ms_batch(self._h, descs, len(mats), out.data_ptr(), _stream_ptr(stream)),
+               "ms_batch")
+        return out
+
+    def batch_descs(self, descs, count: int, out, stream=None):
+        """ms_batch on a prepared ctypes array of ms_matrix (no per-call marshalling)."""
+        _check(lib().ms_batch(self._h, descs, count, out.data_ptr(), _stream_ptr(stream)),
+               "ms_batch")
+        return out
+
+
+def status_string(code: int) -> str:
+    return lib().ms_status_string(code).decode()

@@ -1,0 +1,548 @@
+// libms host side: argument checks, workspace, launch planning and the C ABI
+// declared in include/ms.h.  Device code lives in ms_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ms_kernels.cuh"
+
+using ms::Job;
+using ms::JobState;
+
+struct ms_ctx {
+  int device = 0;
+  size_t budget = 0;  // 0 = unlimited
+  size_t held = 0;    // bytes of device workspace currently held
+  ms_tuning tuning{};
+
+  JobState* d_states = nullptr;
+  int64_t states_cap = 0;
+  uint32_t* d_carry = nullptr;
+  int64_t carry_cap = 0;  // in uint32
+  int32_t* d_progress = nullptr;
+  int64_t progress_cap = 0;
+
+  // batch job table: device copy, the host image it was uploaded from, and a
+  // pinned staging buffer guarded by an event
+  Job* d_jobs = nullptr;
+  int64_t jobs_cap = 0;
+  std::vector<Job> uploaded;
+  Job* h_stage = nullptr;
+  int64_t stage_cap = 0;
+  cudaEvent_t stage_free = nullptr;
+  bool stage_pending = false;
+
+  // kernel timing (ms_profile_start / ms_profile_stop)
+  struct ProfSlot {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  int prof_max = 0;
+  int prof_used = 0;
+  std::vector<ProfSlot> prof_pool;
+  int64_t prof_count[3] = {0, 0, 0};
+  int64_t prof_untimed = 0;
+};
+
+namespace {
+
+constexpr int kTileThreads = 256;
+enum { kProfTile = 0, kProfFixup = 1, kProfOther = 2 };
+
+// Records an event pair around the launches in its scope while profiling is on.
+struct ProfScope {
+  ms_ctx* c;
+  cudaStream_t s;
+  int slot = -1;
+  ProfScope(ms_ctx* ctx, cudaStream_t st, int kind) : c(ctx), s(st) {
+    if (!c || !c->prof_on) return;
+    c->prof_count[kind]++;
+    if (c->prof_used >= c->prof_max) {
+      c->prof_untimed++;
+      return;
+    }
+    if ((int)c->prof_pool.size() <= c->prof_used) {
+      ms_ctx::ProfSlot ps{kind, nullptr, nullptr};
+      if (cudaEventCreate(&ps.a) != cudaSuccess || cudaEventCreate(&ps.b) != cudaSuccess) {
+        cudaGetLastError();
+        c->prof_untimed++;
+        return;
+      }
+      c->prof_pool.push_back(ps);
+    }
+    slot = c->prof_used++;
+    c->prof_pool[slot].kind = kind;
+    cudaEventRecord(c->prof_pool[slot].a, s);
+  }
+  ~ProfScope() {
+    if (slot >= 0) cudaEventRecord(c->prof_pool[slot].b, s);
+  }
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+int choose_P(int64_t n) {
+  if (n <= 32) return 1;
+  if (n <= 64) return 2;
+  if (n <= 128) return 4;
+  if (n <= 256) return 8;
+  return 16;
+}
+
+int64_t strips_for(int64_t n, int P) {
+  const int64_t W = 32 * P;
+  if (n <= W) return 1;
+  return 1 + (n - W + (W - ms::kHalo) - 1) / (W - ms::kHalo);
+}
+
+int64_t fix_strips_for(int64_t n) { return (n + ms::kHalo + ms::kFixW - 1) / ms::kFixW + 1; }
+
+// Rows a tile counts.  A warp walks band_rows + 32 (halo) + 31 (lane skew)
+// steps, so tall bands amortise the halo while short bands give more warps.
+// Aim for about one wave of resident warps (two tiles each) per launch, with
+// bands of at least 32 rows.
+int64_t auto_band_rows_for(int64_t work_rows /* sum of m * strips */) {
+  const int64_t target_tiles = 152 * 8 * 2;
+  int64_t br = (work_rows + target_tiles - 1) / target_tiles;
+  br = ((br + 31) / 32) * 32;
+  br = std::max<int64_t>(br, 32);
+  br = std::min<int64_t>(br, 4096);
+  return br;
+}
+
+int auto_band_rows(int64_t m, int64_t strips) {
+  return (int)std::min<int64_t>(auto_band_rows_for(m * strips), std::max<int64_t>(m, 1));
+}
+
+ms_status check_matrix(const ms_matrix* in) {
+  if (!in) return MS_ERR_INVALID;
+  if (in->m < 0 || in->n < 0) return MS_ERR_INVALID;
+  if (in->fmt != MS_U8 && in->fmt != MS_BITS32) return MS_ERR_INVALID;
+  if (in->reserved != 0) return MS_ERR_INVALID;
+  if (in->m == 0 || in->n == 0) return MS_OK;
+  if (!in->data) return MS_ERR_INVALID;
+  const int64_t row_elems = in->fmt == MS_U8 ? in->n : (in->n + 31) / 32;
+  if (in->ld < row_elems) return MS_ERR_INVALID;
+  if (in->fmt == MS_BITS32 && (reinterpret_cast<uintptr_t>(in->data) & 3u)) return MS_ERR_INVALID;
+  if (in->m > 65000) return MS_ERR_UNSUPPORTED;
+  if (std::min(in->m, in->n) > 32768) return MS_ERR_UNSUPPORTED;
+  if (in->n > ((int64_t)1 << 40) / in->m) return MS_ERR_UNSUPPORTED;
+  return MS_OK;
+}
+
+Job plan_job(const ms_ctx* ctx, const ms_matrix* in) {
+  Job j;
+  std::memset(&j, 0, sizeof(j));
+  j.data = in->data;
+  j.m = in->m;
+  j.n = in->n;
+  j.ld = in->ld;
+  j.fmt = in->fmt;
+  j.P = choose_P(in->n);
+  if (in->m > 0 && in->n > 0) {
+    j.strips = (int32_t)strips_for(in->n, j.P);
+    j.band_rows = ctx->tuning.band_rows > 0 ? (int32_t)std::min<int64_t>(ctx->tuning.band_rows,
+                                                                          in->m)
+                                            : auto_band_rows(in->m, j.strips);
+    j.bands = (int32_t)((in->m + j.band_rows - 1) / j.band_rows);
+  }
+  j.aligned = (in->fmt == MS_U8) && (reinterpret_cast<uintptr_t>(in->data) % 16 == 0) &&
+              (in->ld % 16 == 0);
+  j.strips_fix = (int32_t)fix_strips_for(in->n);
+  return j;
+}
+
+int64_t tiles_of(const Job& j) { return (int64_t)j.bands * j.strips; }
+
+ms_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MS_OK : MS_ERR_CUDA; }
+
+template <typename T>
+void release(ms_ctx* ctx, T*& p, int64_t& cap) {
+  if (p) {
+    cudaFree(p);
+    ctx->held -= (size_t)cap * sizeof(T);
+  }
+  p = nullptr;
+  cap = 0;
+}
+
+template <typename T>
+ms_status grow(ms_ctx* ctx, T*& p, int64_t& cap, int64_t need, bool capture) {
+  if (need <= cap) return MS_OK;
+  if (capture) return MS_ERR_UNSUPPORTED;  // never allocate inside a stream capture
+  int64_t want = std::max<int64_t>(need, cap + cap / 2);
+  const size_t extra = (size_t)(want - cap) * sizeof(T);
+  if (ctx->budget && ctx->held + extra > ctx->budget) {
+    want = need;
+    if (ctx->held + (size_t)(want - cap) * sizeof(T) > ctx->budget) return MS_ERR_OOM;
+  }
+  cudaDeviceSynchronize();  // the old buffer may still be in use
+  release(ctx, p, cap);
+  T* q = nullptr;
+  if (cudaMalloc(&q, (size_t)want * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return MS_ERR_OOM;
+  }
+  p = q;
+  cap = want;
+  ctx->held += (size_t)want * sizeof(T);
+  return MS_OK;
+}
+
+// Device state for `njobs` matrices whose fix-up needs `carry` words and
+// `progress` counters in total.
+ms_status ensure_workspace(ms_ctx* ctx, int64_t njobs, int64_t carry, int64_t progress,
+                           cudaStream_t s) {
+  const bool cap = capturing(s);
+  const int64_t old_states = ctx->states_cap;
+  ms_status st = grow(ctx, ctx->d_states, ctx->states_cap, std::max<int64_t>(njobs, 1), cap);
+  if (st != MS_OK) return st;
+  if (ctx->states_cap != old_states) {
+    const int n = (int)ctx->states_cap;
+    ms::k_init_states<<<(n + 255) / 256, 256>>>(ctx->d_states, n);
+    if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
+  }
+  st = grow(ctx, ctx->d_carry, ctx->carry_cap, std::max<int64_t>(carry, 1), cap);
+  if (st != MS_OK) return st;
+  const int64_t old_prog = ctx->progress_cap;
+  st = grow(ctx, ctx->d_progress, ctx->progress_cap, std::max<int64_t>(progress, 1), cap);
+  if (st != MS_OK) return st;
+  if (ctx->progress_cap != old_prog) {
+    if (cudaMemset(ctx->d_progress, 0, (size_t)ctx->progress_cap * sizeof(int32_t)) != cudaSuccess)
+      return MS_ERR_CUDA;
+  }
+  if (!cap && (ctx->states_cap != old_states || ctx->progress_cap != old_prog)) {
+    if (cudaDeviceSynchronize() != cudaSuccess) return MS_ERR_CUDA;
+  }
+  return MS_OK;
+}
+
+// ---- launches --------------------------------------------------------------
+
+template <int FMT, bool DPMAP>
+cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
+  const int64_t ntiles = tiles_of(j);
+  if (ntiles > 0) {
+    ProfScope ps(ctx, s, kProfTile);
+    const int64_t warps = (ntiles + 1) / 2;
+    const int wpb = kTileThreads / 32;
+    const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
+    switch (j.P) {
+      case 1: ms::k_tiles_one<1, FMT, DPMAP><<<grid, kTileThreads, 0, s>>>(j, ntiles); break;
+      case 2: ms::k_tiles_one<2, FMT, DPMAP><<<grid, kTileThreads, 0, s>>>(j, ntiles); break;
+      case 4: ms::k_tiles_one<4, FMT, DPMAP><<<grid, kTileThreads, 0, s>>>(j, ntiles); break;
+      case 8: ms::k_tiles_one<8, FMT, DPMAP><<<grid, kTileThreads, 0, s>>>(j, ntiles); break;
+      default: ms::k_tiles_one<16, FMT, DPMAP><<<grid, kTileThreads, 0, s>>>(j, ntiles); break;
+    }
+  }
+  {
+    ProfScope ps(ctx, s, kProfFixup);
+    ms::k_fixup_one<FMT, DPMAP><<<1, ms::kFixWarps * 32, 0, s>>>(j);
+  }
+  return cudaGetLastError();
+}
+
+ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_dp,
+                     ms_result* out_dev, cudaStream_t s) {
+  ms_status st = check_matrix(in);
+  if (st != MS_OK) return st;
+  if (!out_dev) return MS_ERR_INVALID;
+  if (dp) {
+    if (in->m > 0 && in->n > 0 && ld_dp < in->n) return MS_ERR_INVALID;
+  }
+  DeviceGuard g(ctx->device);
+  Job j = plan_job(ctx, in);
+  st = ensure_workspace(ctx, 1, j.m * (int64_t)j.strips_fix, j.strips_fix, s);
+  if (st != MS_OK) return st;
+  j.tile0 = 0;
+  j.dp = dp;
+  j.ld_dp = ld_dp;
+  j.dp_aligned = dp && (reinterpret_cast<uintptr_t>(dp) % 16 == 0) && (ld_dp % 4 == 0);
+  j.out = out_dev;
+  j.st = ctx->d_states;
+  j.carry = ctx->d_carry;
+  j.progress = ctx->d_progress;
+  cudaError_t e;
+  if (j.fmt == MS_U8)
+    e = dp ? launch_one_fmt<MS_U8, true>(ctx, j, s) : launch_one_fmt<MS_U8, false>(ctx, j, s);
+  else
+    e = dp ? launch_one_fmt<MS_BITS32, true>(ctx, j, s)
+           : launch_one_fmt<MS_BITS32, false>(ctx, j, s);
+  return cuda_status(e);
+}
+
+template <int FMT>
+cudaError_t launch_group(const Job* d_jobs, int njobs, int64_t ntiles, int P, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  const int64_t warps = (ntiles + 1) / 2;
+  const int wpb = kTileThreads / 32;
+  const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
+  switch (P) {
+    case 1: ms::k_tiles<1, FMT, false><<<grid, kTileThreads, 0, s>>>(d_jobs, njobs, ntiles); break;
+    case 2: ms::k_tiles<2, FMT, false><<<grid, kTileThreads, 0, s>>>(d_jobs, njobs, ntiles); break;
+    case 4: ms::k_tiles<4, FMT, false><<<grid, kTileThreads, 0, s>>>(d_jobs, njobs, ntiles); break;
+    case 8: ms::k_tiles<8, FMT, false><<<grid, kTileThreads, 0, s>>>(d_jobs, njobs, ntiles); break;
+    default: ms::k_tiles<16, FMT, false><<<grid, kTileThreads, 0, s>>>(d_jobs, njobs, ntiles); break;
+  }
+  return cudaGetLastError();
+}
+
+__global__ void k_fixup_mixed(const Job* __restrict__ jobs, int njobs) {
+  const int j = blockIdx.x;
+  if (j >= njobs) return;
+  const Job job = jobs[j];
+  if (job.fmt == MS_U8)
+    ms::fixup_job<MS_U8, false>(job);
+  else
+    ms::fixup_job<MS_BITS32, false>(job);
+}
+
+bool same_jobs(const std::vector<Job>& a, const Job* b, int64_t n) {
+  return (int64_t)a.size() == n && std::memcmp(a.data(), b, (size_t)n * sizeof(Job)) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ms_status_string(ms_status st) {
+  switch (st) {
+    case MS_OK: return "MS_OK";
+    case MS_ERR_INVALID: return "MS_ERR_INVALID: invalid argument";
+    case MS_ERR_OOM: return "MS_ERR_OOM: device memory or workspace budget exhausted";
+    case MS_ERR_CUDA: return "MS_ERR_CUDA: a CUDA runtime call failed";
+    case MS_ERR_TIMEOUT: return "MS_ERR_TIMEOUT: a bounded device-side wait gave up";
+    case MS_ERR_BUDGET: return "MS_ERR_BUDGET: request exceeds the serving memory budget";
+    case MS_ERR_UNSUPPORTED: return "MS_ERR_UNSUPPORTED: outside supported sizes or layouts";
+  }
+  return "unknown ms_status";
+}
+
+ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes) {
+  if (!out) return MS_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return MS_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return MS_ERR_INVALID;
+  ms_ctx* ctx = new (std::nothrow) ms_ctx();
+  if (!ctx) return MS_ERR_OOM;
+  ctx->device = device;
+  ctx->budget = workspace_budget_bytes;
+  DeviceGuard g(device);
+  if (cudaEventCreateWithFlags(&ctx->stage_free, cudaEventDisableTiming) != cudaSuccess) {
+    delete ctx;
+    return MS_ERR_CUDA;
+  }
+  ms_status st = ensure_workspace(ctx, 64, 1 << 16, 1024, nullptr);
+  if (st != MS_OK) {
+    ms_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return MS_OK;
+}
+
+ms_status ms_destroy(ms_ctx* ctx) {
+  if (!ctx) return MS_ERR_INVALID;
+  {
+    DeviceGuard g(ctx->device);
+    cudaDeviceSynchronize();
+    release(ctx, ctx->d_states, ctx->states_cap);
+    release(ctx, ctx->d_carry, ctx->carry_cap);
+    release(ctx, ctx->d_progress, ctx->progress_cap);
+    release(ctx, ctx->d_jobs, ctx->jobs_cap);
+    if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+    if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
+    for (auto& ps : ctx->prof_pool) {
+      cudaEventDestroy(ps.a);
+      cudaEventDestroy(ps.b);
+    }
+  }
+  delete ctx;
+  return MS_OK;
+}
+
+ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t) {
+  if (!ctx || !t) return MS_ERR_INVALID;
+  if (t->band_rows < 0 || t->band_rows > 65000) return MS_ERR_INVALID;
+  ctx->tuning = *t;
+  return MS_OK;
+}
+
+ms_status ms_get_tuning(ms_ctx* ctx, ms_tuning* t) {
+  if (!ctx || !t) return MS_ERR_INVALID;
+  *t = ctx->tuning;
+  return MS_OK;
+}
+
+ms_status ms_max_square(ms_ctx* ctx, const ms_matrix* in, ms_result* out_dev, ms_stream_t s) {
+  if (!ctx) return MS_ERR_INVALID;
+  return run_single(ctx, in, nullptr, 0, out_dev, reinterpret_cast<cudaStream_t>(s));
+}
+
+ms_status ms_dp_map(ms_ctx* ctx, const ms_matrix* in, int32_t* dp_dev, int64_t ld_dp,
+                    ms_result* out_dev, ms_stream_t s) {
+  if (!ctx || !in) return MS_ERR_INVALID;
+  if (!dp_dev && in->m > 0 && in->n > 0) return MS_ERR_INVALID;
+  return run_single(ctx, in, dp_dev, ld_dp, out_dev, reinterpret_cast<cudaStream_t>(s));
+}
+
+ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_result* outs_dev,
+                   ms_stream_t stream) {
+  if (!ctx || count < 0) return MS_ERR_INVALID;
+  if (count == 0) return MS_OK;
+  if (!ins_host || !outs_dev) return MS_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (int32_t i = 0; i < count; ++i) {
+    ms_status st = check_matrix(&ins_host[i]);
+    if (st != MS_OK) return st;
+  }
+  DeviceGuard g(ctx->device);
+  const bool cap = capturing(s);
+
+  // plan: group tiles by (format, columns per lane) so each group is one launch
+  std::vector<Job> jobs((size_t)count);
+  int64_t carry = 0, progress = 0, work = 0;
+  for (int32_t i = 0; i < count; ++i) {
+    jobs[i] = plan_job(ctx, &ins_host[i]);
+    carry += jobs[i].m * (int64_t)jobs[i].strips_fix;
+    progress += jobs[i].strips_fix;
+    work += jobs[i].m * (int64_t)jobs[i].strips;
+  }
+  // one band height for the whole batch, sized on the batch's total work
+  const int64_t br = ctx->tuning.band_rows > 0 ? ctx->tuning.band_rows : auto_band_rows_for(work);
+  for (Job& j : jobs) {
+    if (j.m > 0 && j.n > 0) {
+      j.band_rows = (int32_t)std::min<int64_t>(br, j.m);
+      j.bands = (int32_t)((j.m + j.band_rows - 1) / j.band_rows);
+    }
+  }
+  ms_status st = ensure_workspace(ctx, count, carry, progress, s);
+  if (st != MS_OK) return st;
+  std::vector<int32_t> order((size_t)count);
+  for (int32_t i = 0; i < count; ++i) order[i] = i;
+  auto group_of = [&](const Job& j) { return j.fmt * 8 + __builtin_ctz((unsigned)j.P); };
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return group_of(jobs[a]) < group_of(jobs[b]);
+  });
+  std::vector<Job> table((size_t)count);
+  int64_t carry_off = 0, prog_off = 0;
+  struct Group { int fmt, P, first, count; int64_t ntiles; };
+  std::vector<Group> groups;
+  for (int32_t r = 0; r < count; ++r) {
+    const int32_t i = order[r];
+    Job j = jobs[i];
+    const int gid = group_of(j);
+    if (groups.empty() || group_of(table[groups.back().first]) != gid)
+      groups.push_back(Group{j.fmt, j.P, r, 0, 0});
+    Group& gr = groups.back();
+    j.tile0 = gr.ntiles;
+    gr.ntiles += tiles_of(j);
+    gr.count++;
+    j.out = outs_dev + i;
+    j.st = ctx->d_states + r;
+    j.carry = ctx->d_carry + carry_off;
+    j.progress = ctx->d_progress + prog_off;
+    carry_off += j.m * (int64_t)j.strips_fix;
+    prog_off += j.strips_fix;
+    table[r] = j;
+  }
+
+  // job table upload (skipped when identical to the table already on the device)
+  if (!same_jobs(ctx->uploaded, table.data(), count)) {
+    if (cap) return MS_ERR_UNSUPPORTED;  // first run the call once outside capture
+    st = grow(ctx, ctx->d_jobs, ctx->jobs_cap, count, false);
+    if (st != MS_OK) return st;
+    if (ctx->stage_pending) cudaEventSynchronize(ctx->stage_free);
+    if (ctx->stage_cap < count) {
+      if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
+      ctx->h_stage = nullptr;
+      ctx->stage_cap = 0;
+      if (cudaMallocHost(&ctx->h_stage, (size_t)count * sizeof(Job)) != cudaSuccess) {
+        cudaGetLastError();
+        return MS_ERR_OOM;
+      }
+      ctx->stage_cap = count;
+    }
+    std::memcpy(ctx->h_stage, table.data(), (size_t)count * sizeof(Job));
+    if (cudaMemcpyAsync(ctx->d_jobs, ctx->h_stage, (size_t)count * sizeof(Job),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+      return MS_ERR_CUDA;
+    cudaEventRecord(ctx->stage_free, s);
+    ctx->stage_pending = true;
+    ctx->uploaded = table;
+  }
+
+  for (const Group& gr : groups) {
+    ProfScope ps(ctx, s, kProfTile);
+    cudaError_t e = gr.fmt == MS_U8
+                        ? launch_group<MS_U8>(ctx->d_jobs + gr.first, gr.count, gr.ntiles, gr.P, s)
+                        : launch_group<MS_BITS32>(ctx->d_jobs + gr.first, gr.count, gr.ntiles,
+                                                  gr.P, s);
+    if (e != cudaSuccess) return MS_ERR_CUDA;
+  }
+  {
+    ProfScope ps(ctx, s, kProfFixup);
+    k_fixup_mixed<<<count, ms::kFixWarps * 32, 0, s>>>(ctx->d_jobs, count);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+ms_status ms_profile_start(ms_ctx* ctx, int32_t max_launches) {
+  if (!ctx || max_launches < 0) return MS_ERR_INVALID;
+  ctx->prof_on = true;
+  ctx->prof_max = max_launches;
+  ctx->prof_used = 0;
+  ctx->prof_count[0] = ctx->prof_count[1] = ctx->prof_count[2] = 0;
+  ctx->prof_untimed = 0;
+  return MS_OK;
+}
+
+ms_status ms_profile_stop(ms_ctx* ctx, ms_profile* out) {
+  if (!ctx || !out) return MS_ERR_INVALID;
+  DeviceGuard g(ctx->device);
+  ctx->prof_on = false;
+  double ms_sum[3] = {0, 0, 0};
+  for (int i = 0; i < ctx->prof_used; ++i) {
+    const ms_ctx::ProfSlot& ps = ctx->prof_pool[i];
+    if (cudaEventSynchronize(ps.b) != cudaSuccess) return MS_ERR_CUDA;
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ps.a, ps.b) != cudaSuccess) return MS_ERR_CUDA;
+    ms_sum[ps.kind] += t;
+  }
+  out->tile_launches = ctx->prof_count[kProfTile];
+  out->tile_ms = ms_sum[kProfTile];
+  out->fixup_launches = ctx->prof_count[kProfFixup];
+  out->fixup_ms = ms_sum[kProfFixup];
+  out->other_launches = ctx->prof_count[kProfOther];
+  out->other_ms = ms_sum[kProfOther];
+  out->untimed_launches = ctx->prof_untimed;
+  ctx->prof_used = 0;
+  return MS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+// Device-side building blocks of libms (sm_103a).
+//
+// The method: for every cell, dp[i][j] = side of the largest all-ones square
+// with bottom-right corner (i, j) (Eq. 1, Sec. 2.1); the answer is max dp and
+// the first cell reaching it in row-major order (where the paper's
+// Algorithm 1, Sec. 3.2, makes its last validation).
+//
+// Restatement used on the GPU.  With h = vertical run of ones ending at the
+// cell (the paper's frequency array freq[j], Sec. 3.4) and left = horizontal
+// run ending at the cell (the paper's counter when the threshold is 1),
+//   dp[i][j] = min(dp[i-1][j-1] + 1, h[i][j], left[i][j]).
+// In row units, A = i + 1 - dp, Z = i + 1 - h (one past the last zero row of
+// the column) and Q = i + 1 - left turn the three-way minimum into
+//   A[i][j] = max(A[i-1][j-1], Z[i][j], Q[i][j]),
+// where Z only changes at a zero cell (Z := i + 1) and Q is a chain along the
+// row (Q := Q_left - 1 on a one, i + 1 on a zero).  All three quantities are
+// small non-negative integers kept two per 32-bit register (16x2 SIMD).
+#pragma once
+#include <cstdint>
+
+#include "../../include/ms.h"
+
+namespace ms {
+
+constexpr uint32_t kBias = 64;             // row offset so that every value stays >= 1
+constexpr int kHalo = 32;                  // halo rows above / columns left of a tile
+constexpr uint64_t kKeyMask = (1ull << 40) - 1;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kSpinLimit = 1 << 22;        // bounded waits (x ~100 ns sleep => ~0.4 s)
+
+// ---- per-matrix job description and state ---------------------------------
+
+struct JobState {
+  unsigned long long key;  // (side << 40) | (kKeyMask - (row*n + col)), atomicMax
+  int32_t box[4];          // unresolved region: row lo, row hi, col lo, col hi
+  int32_t status;          // ms_status of device-side problems
+  int32_t pad;
+};
+
+struct Job {
+  const void* data;
+  int64_t m, n, ld;        // ld in bytes (MS_U8) or words (MS_BITS32)
+  int32_t fmt;
+  int32_t P;               // columns per lane in a tile (tile width = 32*P)
+  int32_t band_rows;       // rows a tile counts
+  int32_t bands, strips;
+  int32_t aligned;         // U8: data and ld allow 16-byte vector loads
+  int64_t tile0;           // index of this job's first tile in its launch group
+  int32_t* dp;             // optional dp map (device), may be null
+  int64_t ld_dp;
+  int32_t dp_aligned;      // dp and ld_dp allow 16-byte vector stores
+  int32_t pad;
+  ms_result* out;
+  JobState* st;
+  uint32_t* carry;         // fix-up strip carries: strips_fix rows each
+  int32_t* progress;       // fix-up per-strip published row counts
+  int32_t strips_fix;      // capacity of carry/progress in strips
+  int32_t pad2;
+};
+
+// ---- 16x2 SIMD helpers ---------------------------------------------------
+
+__device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+__device__ __forceinline__ uint32_t vadd2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("add.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+// (a where mask bits are set) | (b elsewhere): one LOP3
+__device__ __forceinline__ uint32_t select_bits(uint32_t a, uint32_t b, uint32_t mask) {
+  return (a & mask) | (b & ~mask);
+}
+// PTX prmt in its default mode, where bit 3 of a selector nibble replicates
+// the sign (most significant bit) of the selected byte across the output byte.
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+  return r;
+}
+// Marks each nonzero byte of x with its most significant bit (other bits are junk).
+__device__ __forceinline__ uint32_t nonzero_msb(uint32_t x) {
+  return ((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x;
+}
+
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// ---- input loading --------------------------------------------------------
+// A lane owns P consecutive columns of a tile row.  Raw<P, FMT> holds them as
+// loaded, with no arithmetic on the loaded value, so that a load issued D
+// steps ahead is not waited for until its row is consumed.
+// MS_U8: ceil(P/4) words of bytes; MS_BITS32: the 32-bit word holding them.
+
+template <int P, int FMT>
+struct Raw;
+
+template <int P>
+struct Raw<P, MS_U8> {
+  static constexpr int W = (P + 3) / 4;
+  uint32_t w[W];
+};
+template <int P>
+struct Raw<P, MS_BITS32> {
+  uint32_t word;
+};
+
+template <int P>
+__device__ __forceinline__ void load_u8(Raw<P, MS_U8>& r, const uint8_t* row, int64_t col,
+                                        int64_t n, bool aligned) {
+#pragma unroll
+  for (int i = 0; i < Raw<P, MS_U8>::W; ++i) r.w[i] = 0;
+  if (col >= n) return;
+  if (aligned && col + P <= n) {
+    const uint8_t* p = row + col;
+    if constexpr (P == 16) {
+      uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+      r.w[0] = v.x; r.w[1] = v.y; r.w[2] = v.z; r.w[3] = v.w;
+    } else if constexpr (P == 8) {
+      uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+      r.w[0] = v.x; r.w[1] = v.y;
+    } else if constexpr (P == 4) {
+      r.w[0] = __ldg(reinterpret_cast<const uint32_t*>(p));
+    } else if constexpr (P == 2) {
+      r.w[0] = __ldg(reinterpret_cast<const uint16_t*>(p));
+    } else {
+      r.w[0] = __ldg(p);
+    }
+  } else {
+    // edge or unaligned chunk: byte loads (this path waits for its loads)
+#pragma unroll
+    for (int b = 0; b < P; ++b)
+      if (col + b < n) r.w[b >> 2] |= (uint32_t)__ldg(row + col + b) << (8 * (b & 3));
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void load_bits(Raw<P, MS_BITS32>& r, const uint32_t* row, int64_t col,
+                                          int64_t n) {
+  static_assert(P <= 16, "two tiles share a register: at most 16 columns per lane");
+  r.word = 0;
+  if (col >= n) return;
+  r.word = __ldg(row + (col >> 5));
+}
+
+// Per-lane constants that turn a Raw into cells: for MS_BITS32 the shift of
+// the lane's columns inside their word and the mask of columns < n.
+struct LaneCols {
+  uint32_t shift;
+  uint32_t mask;
+};
+template <int P>
+__device__ __forceinline__ LaneCols lane_cols(int64_t col, int64_t n) {
+  LaneCols c;
+  c.shift = (uint32_t)(col & 31);
+  const int64_t valid = n - col;
+  c.mask = valid <= 0 ? 0u : (valid >= P ? ((1u << P) - 1u) : ((1u << valid) - 1u));
+  return c;
+}
+
+// Cells ready for pair_mask: MS_U8 words with each nonzero byte marked in its
+// most significant bit, MS_BITS32 the lane's P bits in the low bits.
+template <int P, int FMT>
+struct Cells;
+template <int P>
+struct Cells<P, MS_U8> {
+  uint32_t w[Raw<P, MS_U8>::W];
+};
+template <int P>
+struct Cells<P, MS_BITS32> {
+  uint32_t bits;
+};
+
+template <int P>
+__device__ __forceinline__ Cells<P, MS_U8> cells_of(const Raw<P, MS_U8>& r, const LaneCols&) {
+  Cells<P, MS_U8> c;
+#pragma unroll
+  for (int i = 0; i < Raw<P, MS_U8>::W; ++i) c.w[i] = nonzero_msb(r.w[i]);
+  return c;
+}
+template <int P>
+__device__ __forceinline__ Cells<P, MS_BITS32> cells_of(const Raw<P, MS_BITS32>& r,
+                                                        const LaneCols& lc) {
+  Cells<P, MS_BITS32> c;
+  c.bits = (r.word >> lc.shift) & lc.mask;
+  return c;
+}
+
+// 16x2 mask of pair k: low half 0xffff if the low tile's cell is one, high
+// half 0xffff if the high tile's cell is one.
+template <int P>
+__device__ __forceinline__ uint32_t pair_mask(const Cells<P, MS_U8>& lo,
+                                              const Cells<P, MS_U8>& hi, int k) {
+  const uint32_t b = (uint32_t)(k & 3);
+  const uint32_t sel = (8u | b) | ((8u | b) << 4) | ((12u | b) << 8) | ((12u | b) << 12);
+  return prmt(lo.w[k >> 2], hi.w[k >> 2], sel);
+}
+template <int P>
+__device__ __forceinline__ uint32_t pair_mask(const Cells<P, MS_BITS32>& lo,
+                                              const Cells<P, MS_BITS32>& hi, int k) {
+  const uint32_t w = (lo.bits & 0xffffu) | (hi.bits << 16);
+  return prmt(w << (15 - k), 0u, 0xBB99u);
+}
+
+// ---- results --------------------------------------------------------------
+
+struct Best {
+  int32_t val;
+  int32_t row;
+  int32_t col;
+};
+
+__device__ __forceinline__ unsigned long long make_key(int32_t val, int64_t row, int64_t col,
+                                                       int64_t n) {
+  if (val <= 0) return 0ull;
+  return ((unsigned long long)val << 40) |
+         (kKeyMask - (unsigned long long)(row * n + col));
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    unsigned long long o = __shfl_xor_sync(kFull, v, d);
+    v = o > v ? o : v;
+  }
+  return v;
+}
+
+}  // namespace ms

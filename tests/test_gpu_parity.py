@@ -1,0 +1,227 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, bit for
+bit (all results are integers).  Inputs come from the seeded generator."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ms():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2503_18974_gb300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(ms):
+    c = ms.MaxSquare(0)
+    yield c
+    c.close()
+
+
+DEV = "cuda:0"
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def bits_dev(a, n, pad=0, ldw=None):
+    w = gen.pack_bits(a, n, ldw=ldw, pad_value=pad)
+    return torch.from_numpy(w.view(np.int32)).to(DEV)
+
+
+def run_all_paths(ctx, a, check_map=True, pads=(0, 1)):
+    """Every entry point on matrix a (uint8, m x n) against the oracle."""
+    m, n = a.shape
+    (K, r, c), dref = oracle.dp(a)
+    exp = [K, r, c, 0]
+    x = to_dev(a)
+    assert ctx.max_square(x).cpu().tolist() == exp, ("u8", m, n)
+    if check_map:
+        dp, res = ctx.dp_map(x)
+        assert res.cpu().tolist() == exp, ("u8 map", m, n)
+        assert np.array_equal(dp.cpu().numpy(), dref), ("u8 map values", m, n)
+    for pad in pads:
+        w = bits_dev(a, n, pad=pad)
+        assert ctx.max_square(w, n=n).cpu().tolist() == exp, ("bits", m, n, pad)
+        if check_map:
+            dp, res = ctx.dp_map(w, n=n)
+            assert res.cpu().tolist() == exp, ("bits map", m, n, pad)
+            assert np.array_equal(dp.cpu().numpy(), dref), ("bits map values", m, n, pad)
+    return K, r, c
+
+
+SHAPES = [(1, 1), (1, 7), (7, 1), (2, 2), (31, 33), (32, 32), (33, 31), (64, 65), (100, 127),
+          (129, 128), (255, 257), (300, 512), (257, 513), (70, 992), (40, 993), (33, 1505),
+          (520, 700), (1000, 1100)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("p", [0.3, 0.8, 0.95])
+def test_random_shapes(ctx, shape, p):
+    m, n = shape
+    a = gen.bernoulli_u8(m, n, p, seed=m * 1000 + n + int(p * 100))
+    run_all_paths(ctx, a)
+
+
+@pytest.mark.parametrize("band_rows", [32, 64, 96])
+def test_many_bands_and_planted_squares_cross_tiles(ctx, band_rows):
+    """Small bands force many tiles; planted squares larger than the 32-cell
+    halo straddle tile rows and strips, so the exact fix-up runs."""
+    ctx.set_tuning(band_rows=band_rows)
+    try:
+        rng = np.random.default_rng(band_rows)
+        for t in range(6):
+            m, n = int(rng.integers(200, 700)), int(rng.integers(400, 2200))
+            a = gen.bernoulli_u8(m, n, 0.9, seed=100 + t)
+            for s in [40, 75, int(rng.integers(33, min(m, n)))]:
+                r0, c0 = int(rng.integers(0, m - s + 1)), int(rng.integers(0, n - s + 1))
+                a[r0:r0 + s, c0:c0 + s] = 1
+            run_all_paths(ctx, a, pads=(1,))
+    finally:
+        ctx.set_tuning(band_rows=0)
+
+
+def test_squares_on_tile_edges(ctx):
+    ctx.set_tuning(band_rows=64)
+    try:
+        n = 2000
+        for (r0, c0, s) in [(0, 0, 64), (63, 511, 33), (64, 512, 40), (31, 480, 100),
+                            (100, 991, 34), (127, 1471, 65), (190, 960, 200)]:
+            a = gen.bernoulli_u8(400, n, 0.6, seed=r0 + c0 + s)
+            a[r0:r0 + s, c0:c0 + s] = 1
+            run_all_paths(ctx, a, pads=(0,))
+    finally:
+        ctx.set_tuning(band_rows=0)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 600), (600, 1), (5, 9), (512, 512), (700, 1500),
+                                   (2000, 1300)])
+def test_closed_forms(ctx, shape):
+    m, n = shape
+    s = min(m, n)
+    ones = np.ones((m, n), dtype=np.uint8)
+    K = run_all_paths(ctx, ones, check_map=(m * n <= 1_000_000))
+    assert K == (s, s - 1, s - 1)
+    zeros = np.zeros((m, n), dtype=np.uint8)
+    assert run_all_paths(ctx, zeros, check_map=False) == (0, -1, -1)
+    one = zeros.copy()
+    one[m // 2, n // 3] = 1
+    assert run_all_paths(ctx, one, check_map=False) == (1, m // 2, n // 3)
+    ii, jj = np.meshgrid(np.arange(m), np.arange(n), indexing="ij")
+    chk = ((ii + jj) % 2 == 1).astype(np.uint8)
+    if m * n > 1:
+        exp = (1, 0, 1) if n > 1 else (1, 1, 0)
+        assert run_all_paths(ctx, chk, check_map=False) == exp
+
+
+def test_all_ones_large_uses_fixup_everywhere(ctx):
+    m, n = 4096, 3000
+    x = torch.ones((m, n), dtype=torch.uint8, device=DEV)
+    assert ctx.max_square(x).cpu().tolist() == [3000, 2999, 2999, 0]
+    dp, res = ctx.dp_map(x)
+    assert res.cpu().tolist() == [3000, 2999, 2999, 0]
+    ii = torch.arange(m, device=DEV).view(-1, 1)
+    jj = torch.arange(n, device=DEV).view(1, -1)
+    assert torch.equal(dp, torch.minimum(ii, jj).to(torch.int32) + 1)
+
+
+def test_empty_matrices(ctx):
+    for shp in [(0, 5), (5, 0), (0, 0)]:
+        x = torch.zeros(shp, dtype=torch.uint8, device=DEV)
+        assert ctx.max_square(x).cpu().tolist() == [0, -1, -1, 0]
+        dp, res = ctx.dp_map(x)
+        assert res.cpu().tolist() == [0, -1, -1, 0]
+
+
+def test_nonzero_bytes_and_strides(ctx):
+    rng = np.random.default_rng(3)
+    a = (rng.random((300, 900)) < 0.9).astype(np.uint8)
+    a[50:120, 200:270] = 1
+    vals = a * rng.integers(1, 256, size=a.shape).astype(np.uint8)
+    (K, r, c), dref = oracle.dp(a)
+    # ld not a multiple of 16, and a column-offset view (unaligned base)
+    big = torch.zeros((300, 1003), dtype=torch.uint8, device=DEV)
+    big[:, 3:903] = to_dev(vals)
+    view = big[:, 3:903]
+    assert ctx.max_square(view).cpu().tolist() == [K, r, c, 0]
+    dp, res = ctx.dp_map(view)
+    assert np.array_equal(dp.cpu().numpy(), dref)
+    # dp map written with a padded row stride
+    dpbig = torch.full((300, 907), -7, dtype=torch.int32, device=DEV)
+    ctx.dp_map(view, dp=dpbig[:, :900])
+    assert np.array_equal(dpbig[:, :900].cpu().numpy(), dref)
+    assert (dpbig[:, 900:] == -7).all()
+    # packed rows with extra words per row (ldw > ceil(n/32)) and pad bits set
+    w = bits_dev(a, 900, pad=1, ldw=40)
+    assert ctx.max_square(w, n=900).cpu().tolist() == [K, r, c, 0]
+
+
+def test_generated_c1_with_dp_map(ctx):
+    """256 x 256, Bernoulli(0.5), seed 0: side, witness and the full dp map."""
+    a = gen.bernoulli_u8(256, 256, 0.5, seed=0)
+    K = run_all_paths(ctx, a)
+    assert oracle.freq(a) == K
+
+
+def test_batch_mixed_shapes_and_formats(ctx):
+    rng = np.random.default_rng(11)
+    mats, exps, singles = [], [], []
+    for i in range(60):
+        m = int(np.exp(rng.uniform(np.log(1), np.log(900))))
+        n = int(np.exp(rng.uniform(np.log(1), np.log(1500))))
+        p = float(rng.choice(np.arange(1, 10) / 10))
+        a = gen.bernoulli_u8(m, n, p, seed=500 + i)
+        if i % 2 and min(m, n) > 1:
+            s = int(rng.integers(1, min(m, n) + 1))
+            r0, c0 = gen.plant_pos(500 + i, m, n, s)
+            a[r0:r0 + s, c0:c0 + s] = 1
+        (K, r, c), _ = oracle.dp(a, want_map=False)
+        exps.append([K, r, c, 0])
+        if i % 3 == 0:
+            mats.append((bits_dev(a, n, pad=i % 2), n))
+        else:
+            mats.append(to_dev(a))
+    out = ctx.batch(mats).cpu().tolist()
+    assert out == exps
+    # each result alone equals its result in the mix
+    for i, item in enumerate(mats[:20]):
+        res = ctx.max_square(*item) if isinstance(item, tuple) else ctx.max_square(item)
+        assert res.cpu().tolist() == out[i]
+    # repeated call (job table reused) and CUDA-graph capture of the same call
+    assert ctx.batch(mats).cpu().tolist() == exps
+    outbuf = torch.empty((len(mats), 4), dtype=torch.int32, device=DEV)
+    ctx.batch(mats, out=outbuf)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            ctx.batch(mats, out=outbuf)
+    outbuf.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert outbuf.cpu().tolist() == exps
+
+
+def test_invalid_arguments(ctx, ms):
+    x = torch.zeros((10, 10), dtype=torch.uint8, device=DEV)
+    desc = ms.describe(x)
+    desc.ld = 5
+    assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), x.data_ptr(), None) == 1
+    desc = ms.describe(x)
+    desc.fmt = 7
+    assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), x.data_ptr(), None) == 1
+    desc = ms.describe(x)
+    desc.m = 70000
+    assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), x.data_ptr(), None) == 6
+    desc = ms.describe(x)
+    assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), None, None) == 1
