@@ -17,6 +17,7 @@ Workloads (sizes from the configurations this benchmark mirrors):
   c1       256 x 256, p = 0.5, seed 0, side + witness + int32 dp map
   c3-u8 / c3-u8-dp / c3-bits / c3-bits-dp
            32768 x 32768, p = 0.9, one planted 600-square, seed 3
+  c3q-*    the same with 8192 rows (for profiler captures)
   c4       4096 uint8 matrices, m and n log-uniform in [16, 2048], one ms_batch
 """
 from __future__ import annotations
@@ -183,10 +184,13 @@ def make_workload(name, device, host=False):
     if name.startswith("c3"):
         fmt = 1 if "bits" in name else 0
         dp = name.endswith("-dp")
-        return PlainSet(device, [c3_spec()], fmt=fmt, dpmap=dp,
-                        label=f"32768x32768 {'bit-packed' if fmt else 'uint8'}, p=0.9, planted "
-                              f"600-square, seed 3, {'dp map' if dp else 'side + witness'}",
-                        host=host)
+        spec = c3_spec()
+        if name.startswith("c3q"):  # a quarter of it (8192 rows) for profiler captures
+            spec = dict(spec, m=8192)
+        return PlainSet(device, [spec], fmt=fmt, dpmap=dp,
+                        label=f"{spec['m']}x32768 {'bit-packed' if fmt else 'uint8'}, p=0.9, "
+                              f"planted 600-square, seed 3, "
+                              f"{'dp map' if dp else 'side + witness'}", host=host)
     if name == "c4":
         return PlainSet(device, c4_specs(), label="batch of 4096 uint8 matrices, m,n "
                         "log-uniform in [16,2048], p in 0.1..0.9, half planted", host=host)
