@@ -108,6 +108,27 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
 /* Free the context and its workspace (after synchronising its device work). */
 ms_status ms_destroy(ms_ctx* ctx);
 
+/* ms_max_square for callers that may not allocate device memory.  The paper
+ * has no counterpart: this is a library convenience.  Some callers cannot
+ * call cudaMalloc, for example plug-ins inside an application whose own pool
+ * allocator owns all device memory, or latency-critical services that must
+ * not allocate after start-up because an allocation can synchronise the
+ * device.  Such callers cannot create an ms_ctx, so this call needs none and
+ * allocates nothing: it computes the same result as ms_max_square into
+ * out_dev (one ms_result in device memory), using a fixed scratch array of
+ * about 0.6 MiB that lives in the library's device image on every GPU that
+ * loads the library, until the process exits.
+ * - Limits: m <= 8192 and n <= 8192 (MS_U8 or MS_BITS32); a larger matrix
+ *   returns MS_ERR_UNSUPPORTED and launches nothing.
+ * - The first call on each device looks up the scratch array's device
+ *   address (cudaGetSymbolAddress, with that device current); make that
+ *   first call before any stream capture on that device.
+ * - Every call on a device shares the one scratch array and clears the parts
+ *   that must start at zero.  Calls whose work overlaps on the GPU (other
+ *   streams, other host threads) race on it and give wrong results: order
+ *   them on one stream or synchronise between them. */
+ms_status ms_max_square_noalloc(const ms_matrix* in, ms_result* out_dev, ms_stream_t s);
+
 /* Static, human-readable name of a status code. */
 const char* ms_status_string(ms_status st);
 

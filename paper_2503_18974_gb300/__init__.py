@@ -19,8 +19,9 @@ from typing import Iterable, Sequence
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libms.so")
-_SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_kernels.cuh", "ms_device.cuh",
-                                                      "ms_bits.cuh")]
+_SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu", "ms_kernels.cuh",
+                                                      "ms_device.cuh", "ms_bits.cuh")]
+_UNITS = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu")]
 _HEADER = os.path.join(_ROOT, "include", "ms.h")
 
 MS_U8 = 0
@@ -44,7 +45,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     stale = force or not os.path.exists(LIB_PATH) or any(
         os.path.getmtime(p) > os.path.getmtime(LIB_PATH) for p in srcs)
     if stale:
-        cmd = ["nvcc", *NVCC_FLAGS, "-o", LIB_PATH, os.path.join(_HERE, "csrc", "ms.cu")]
+        cmd = ["nvcc", *NVCC_FLAGS, "-o", LIB_PATH, *_UNITS]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         subprocess.check_call(cmd)

@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup_one(const Job job) {
   fixup_job<FMT, DPMAP>(job);
 }
 
-__global__ void k_init_states(JobState* st, int n) {
+static __global__ void k_init_states(JobState* st, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     st[i].key = 0ull;
