@@ -116,7 +116,7 @@ ms_status ms_destroy(ms_ctx* ctx);
  * device.  Such callers cannot create an ms_ctx, so this call needs none and
  * allocates nothing: it computes the same result as ms_max_square into
  * out_dev (one ms_result in device memory), using a fixed scratch array of
- * about 0.6 MiB that lives in the library's device image on every GPU that
+ * about 1.1 MiB that lives in the library's device image on every GPU that
  * loads the library, until the process exits.
  * - Limits: m <= 8192 and n <= 8192 (MS_U8 or MS_BITS32); a larger matrix
  *   returns MS_ERR_UNSUPPORTED and launches nothing.

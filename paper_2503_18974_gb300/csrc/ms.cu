@@ -120,10 +120,10 @@ int64_t fix_strips_for(int64_t n) { return (n + ms::kHalo + ms::kFixW - 1) / ms:
 
 // Rows a tile counts.  A warp walks band_rows + 32 (halo) + 31 (lane skew)
 // steps, so tall bands amortise the halo while short bands give more warps.
-// Aim for about one wave of resident warps (two tiles each) per launch, with
-// bands of at least 32 rows.
+// Aim for about one wave of resident warps (16 per SM, two tiles each) per
+// launch, with bands of at least 32 rows.
 int64_t auto_band_rows_for(int64_t work_rows /* sum of m * strips */) {
-  const int64_t target_tiles = 152 * 8 * 2;
+  const int64_t target_tiles = 152 * 16 * 2;
   int64_t br = (work_rows + target_tiles - 1) / target_tiles;
   br = ((br + 31) / 32) * 32;
   br = std::max<int64_t>(br, 32);

@@ -122,44 +122,6 @@ struct Raw<P, MS_BITS32> {
   uint32_t word;
 };
 
-template <int P>
-__device__ __forceinline__ void load_u8(Raw<P, MS_U8>& r, const uint8_t* row, int64_t col,
-                                        int64_t n, bool aligned) {
-#pragma unroll
-  for (int i = 0; i < Raw<P, MS_U8>::W; ++i) r.w[i] = 0;
-  if (col >= n) return;
-  if (aligned && col + P <= n) {
-    const uint8_t* p = row + col;
-    if constexpr (P == 16) {
-      uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
-      r.w[0] = v.x; r.w[1] = v.y; r.w[2] = v.z; r.w[3] = v.w;
-    } else if constexpr (P == 8) {
-      uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
-      r.w[0] = v.x; r.w[1] = v.y;
-    } else if constexpr (P == 4) {
-      r.w[0] = __ldg(reinterpret_cast<const uint32_t*>(p));
-    } else if constexpr (P == 2) {
-      r.w[0] = __ldg(reinterpret_cast<const uint16_t*>(p));
-    } else {
-      r.w[0] = __ldg(p);
-    }
-  } else {
-    // edge or unaligned chunk: byte loads (this path waits for its loads)
-#pragma unroll
-    for (int b = 0; b < P; ++b)
-      if (col + b < n) r.w[b >> 2] |= (uint32_t)__ldg(row + col + b) << (8 * (b & 3));
-  }
-}
-
-template <int P>
-__device__ __forceinline__ void load_bits(Raw<P, MS_BITS32>& r, const uint32_t* row, int64_t col,
-                                          int64_t n) {
-  static_assert(P <= 16, "two tiles share a register: at most 16 columns per lane");
-  r.word = 0;
-  if (col >= n) return;
-  r.word = __ldg(row + (col >> 5));
-}
-
 // Per-lane constants that turn a Raw into cells: for MS_BITS32 the shift of
 // the lane's columns inside their word and the mask of columns < n.
 struct LaneCols {
@@ -222,9 +184,11 @@ __device__ __forceinline__ uint32_t pair_mask(const Cells<P, MS_BITS32>& lo,
 // ---- results --------------------------------------------------------------
 
 struct Best {
-  int32_t val;
+  int32_t val;  // largest dp seen, its first position
   int32_t row;
   int32_t col;
+  int32_t big_r0, big_r1;  // rows holding a dp above the halo (big_r0 = INT_MAX: none)
+  int64_t big_c0, big_c1;  // columns of the lane chunks holding one
 };
 
 __device__ __forceinline__ unsigned long long make_key(int32_t val, int64_t row, int64_t col,

@@ -8,26 +8,26 @@
 // carries (as if the window's outside were zeros).  Inside such a window the
 // recurrence yields dp_w = min(dp, rows into the window, columns into the
 // window), so every counted cell is exact as soon as the tile's largest dp_w
-// is at most the halo.  Tiles whose largest value exceeds the halo are
-// "flagged" and their union is recorded as a bounding box per matrix.  Tiles
-// on the matrix's top or left edge are exact whatever their values, but they
-// are flagged all the same: the fix-up below relies on every unflagged cell
-// having dp <= halo.
+// is at most the halo.  Cells whose value exceeds the halo are "flagged"
+// and their bounding box (rows exact, columns rounded out to a lane's chunk)
+// is recorded per matrix.  Cells on the matrix's top or left edge are exact
+// whatever their values, but they are flagged all the same: the fix-up below
+// relies on every unflagged cell having dp <= halo.
 //
 // Lanes are skewed by one row: at step s lane l works on window row s - l,
 // so what lane l needs from lane l-1 (the row's horizontal run carry Q and
 // the diagonal A of the previous row) was produced one step earlier and is
 // passed with two shuffles; nothing waits inside a step.
 //
-// Fix-up.  If a matrix has unresolved tiles, the box [rlo, rhi) x [clo, chi)
+// Fix-up.  If a matrix has flagged cells, their box [rlo, rhi) x [clo, chi)
 // grown by the halo up and left is recomputed exactly as one window: its
-// columns are split into strips of 512, one warp per strip, and each strip
+// columns are split into strips of kFixW, one warp per strip, and each strip
 // takes the exact horizontal carry of its left neighbour row by row through
 // global memory (release/acquire flags, bounded waits).  A square whose
 // corner lies in the box and which reached above the grown window would
-// contain a square of side > halo ending on the row just above rlo, whose
-// tile would then be flagged too (likewise on the left); so every cell of
-// the box is exact.
+// contain a square of side > halo ending on the row just above rlo, and that
+// cell, whose window value is at least min(dp, halo + 1), would then be
+// flagged too (likewise on the left); so every cell of the box is exact.
 #pragma once
 #include "ms_device.cuh"
 
@@ -83,25 +83,63 @@ __device__ __forceinline__ Tile empty_tile() {
   return g;
 }
 
+// Streams one lane's column chunk of a tile down the window, one row per
+// call, with the address and the bounds decisions fixed once per tile.
 template <int P, int FMT>
-__device__ __forceinline__ void load_row(Raw<P, FMT>& r, const Tile& g, int ir, int lane) {
-  const int64_t col = g.wc0 + (int64_t)P * lane;
-  if (ir < 0 || ir >= g.nrows) {
+struct LaneReader {
+  const uint8_t* ptr;  // chunk of window row `row`
+  int64_t stride;      // bytes between rows
+  int row, nrows;
+  int mode;            // 0: no cells, 1: full aligned chunk, 2: edge or unaligned chunk
+  int nvalid;          // mode 2: cells of the chunk left of column n
+
+  __device__ __forceinline__ void init(const Tile& g, int lane, int first_row) {
+    const int64_t col = g.wc0 + (int64_t)P * lane;
+    row = first_row;
+    nrows = g.nrows;
+    if constexpr (FMT == MS_U8) {
+      stride = g.ld;
+      ptr = g.base + (g.wr0 + first_row) * g.ld + col;
+      const int64_t valid = g.n - col;
+      nvalid = (int)(valid < P ? (valid < 0 ? 0 : valid) : P);
+      mode = nvalid == 0 ? 0 : ((nvalid == P && g.aligned) ? 1 : 2);
+    } else {
+      stride = g.ld * 4;
+      ptr = g.base + ((g.wr0 + first_row) * g.ld + (col >> 5)) * 4;
+      nvalid = 0;
+      mode = col < g.n ? 1 : 0;
+    }
+  }
+
+  __device__ __forceinline__ void next(Raw<P, FMT>& r) {
+    const bool ok = (unsigned)row < (unsigned)nrows;
     if constexpr (FMT == MS_U8) {
 #pragma unroll
-      for (int i = 0; i < Raw<P, FMT>::W; ++i) r.w[i] = 0;
+      for (int i = 0; i < Raw<P, MS_U8>::W; ++i) r.w[i] = 0;
+      if (ok && mode == 1) {
+        if constexpr (P == 16) {
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(ptr));
+          r.w[0] = v.x; r.w[1] = v.y; r.w[2] = v.z; r.w[3] = v.w;
+        } else if constexpr (P == 8) {
+          const uint2 v = __ldg(reinterpret_cast<const uint2*>(ptr));
+          r.w[0] = v.x; r.w[1] = v.y;
+        } else if constexpr (P == 4) {
+          r.w[0] = __ldg(reinterpret_cast<const uint32_t*>(ptr));
+        } else if constexpr (P == 2) {
+          r.w[0] = __ldg(reinterpret_cast<const uint16_t*>(ptr));
+        } else {
+          r.w[0] = __ldg(ptr);
+        }
+      } else if (ok && mode == 2) {
+        for (int b = 0; b < nvalid; ++b) r.w[b >> 2] |= (uint32_t)__ldg(ptr + b) << (8 * (b & 3));
+      }
     } else {
-      r.word = 0;
+      r.word = (ok && mode == 1) ? __ldg(reinterpret_cast<const uint32_t*>(ptr)) : 0u;
     }
-    return;
+    ptr += stride;
+    ++row;
   }
-  const int64_t row = g.wr0 + ir;
-  if constexpr (FMT == MS_U8) {
-    load_u8<P>(r, g.base + row * g.ld, col, g.n, g.aligned != 0);
-  } else {
-    load_bits<P>(r, reinterpret_cast<const uint32_t*>(g.base) + row * g.ld, col, g.n);
-  }
-}
+};
 
 // Left-edge carries of a strip in the fix-up (mode 1).
 struct StripIO {
@@ -112,6 +150,33 @@ struct StripIO {
   int32_t* status;
 };
 
+// Writes one lane's dp values of one row (half `hi` of the packed A values).
+template <int P, bool HI>
+__device__ __forceinline__ void store_dp(int32_t* p, const uint32_t* Ap, uint32_t I, int64_t col,
+                                         int64_t n, int aligned) {
+  auto val = [&](int k) -> int {
+    return (int)I - (int)(HI ? (Ap[k] >> 16) : (Ap[k] & 0xffffu));
+  };
+  if (aligned && col + P <= n && (P % 4) == 0) {
+#pragma unroll
+    for (int k = 0; k < P; k += 4) {
+      int4 v;
+      v.x = val(k);
+      v.y = val(k + 1);
+      v.z = val(k + 2);
+      v.w = val(k + 3);
+      __stcs(reinterpret_cast<int4*>(p + k), v);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+      if (col + k < n) p[k] = val(k);
+  }
+}
+
+// Two independent tiles (low and high 16-bit halves), lanes skewed by a row.
+// Mode 0: tile pass (zero carries on the window edges).  Mode 1: a fix-up
+// strip taking its left carries from `io` and publishing its right ones.
 template <int P, int FMT, bool DPMAP, int MODE>
 __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_t* dpa,
                                           int64_t lda, int dpa_al, int32_t* dpb, int64_t ldb,
@@ -134,18 +199,32 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
   bool gave_up = false;
   ba.val = bb.val = 0;
   ba.row = ba.col = bb.row = bb.col = -1;
+  ba.big_r0 = bb.big_r0 = 0x7fffffff;
+  ba.big_r1 = bb.big_r1 = -1;
+  ba.big_c0 = bb.big_c0 = 0x7fffffffffffffffll;
+  ba.big_c1 = bb.big_c1 = -1;
+  uint32_t best2 = 0;  // best dp per half so far (packed)
+  constexpr uint32_t kHalo2 = (uint32_t)kHalo * 0x10001u;
   const int64_t cola = ta.wc0 + (int64_t)P * lane;
   const int64_t colb = tb.wc0 + (int64_t)P * lane;
-  const bool cnt_cola = cola >= ta.c0 && cola < ta.n;
-  const bool cnt_colb = colb >= tb.c0 && colb < tb.n;
+  // a lane chunk counts when it reaches a counted column: in the fix-up the
+  // box edge need not fall on a chunk edge, and the chunk's cells left of it
+  // are exact too (the window starts at least kHalo columns further left)
+  const uint32_t colmask2 = ((cola + P > ta.c0 && cola < ta.n) ? 0x0000ffffu : 0u) |
+                            ((colb + P > tb.c0 && colb < tb.n) ? 0xffff0000u : 0u);
   const LaneCols lca = lane_cols<P>(cola, ta.n);
   const LaneCols lcb = lane_cols<P>(colb, tb.n);
+  int32_t* dprow_a = DPMAP && dpa ? dpa + ta.wr0 * lda + cola : nullptr;
+  int32_t* dprow_b = DPMAP && dpb ? dpb + tb.wr0 * ldb + colb : nullptr;
 
+  LaneReader<P, FMT> rda, rdb;
+  rda.init(ta, lane, -lane);
+  rdb.init(tb, lane, -lane);
   Raw<P, FMT> lo[D], hi[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    load_row<P, FMT>(lo[d], ta, d - lane, lane);
-    load_row<P, FMT>(hi[d], tb, d - lane, lane);
+    rda.next(lo[d]);
+    rdb.next(hi[d]);
   }
 
   for (int s0 = 0; s0 < nsteps; s0 += D) {
@@ -157,9 +236,9 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
       uint32_t an = __shfl_up_sync(kFull, pubA, 1);
       const Cells<P, FMT> clo = cells_of<P>(lo[d], lca);
       const Cells<P, FMT> chi = cells_of<P>(hi[d], lcb);
-      load_row<P, FMT>(lo[d], ta, ir + D, lane);
-      load_row<P, FMT>(hi[d], tb, ir + D, lane);
-      if (ir >= 0 && ir < nmax) {
+      rda.next(lo[d]);
+      rdb.next(hi[d]);
+      if ((unsigned)ir < (unsigned)nmax) {
         const uint32_t I = (uint32_t)ir + 1u + kBias;
         const uint32_t I2 = I * 0x10001u;
         if (lane == 0) {
@@ -186,14 +265,15 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
             }
           }
         }
-        qn = vmax2(qn, kClamp2);
-        uint32_t Q = qn, Ad = an, rmin = 0xffffffffu;
+        // Q >= kBias - 1 keeps every half >= 1 through the chain below, so the
+        // packed decrement by 0x00010001 never borrows across halves.
+        uint32_t Q = vmax2(qn, kClamp2), Ad = an, rmin = 0xffffffffu;
 #pragma unroll
         for (int k = 0; k < P; ++k) {
           const uint32_t msk = pair_mask<P>(clo, chi, k);
           const uint32_t zk = select_bits(Z[k], I2, msk);
           Z[k] = zk;
-          Q = select_bits(vadd2(Q, 0xffffffffu), I2, msk);
+          Q = select_bits(Q - 0x00010001u, I2, msk);
           const uint32_t an_k = vmax2(vmax2(Ad, zk), Q);
           Ad = Ap[k];
           Ap[k] = an_k;
@@ -205,78 +285,67 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
         if constexpr (MODE == 1) {
           if (lane == 31 && io.carry_out) {
             io.carry_out[ir] = (Q & 0xffffu) | (Ap[P - 1] << 16);
-            if (((ir + 1) & 31) == 0 || ir + 1 == ta.nrows) {
+            if (((ir + 1) & 7) == 0 || ir + 1 == ta.nrows) {
               __threadfence();
               st_release(io.progress_out, ir + 1);
             }
           }
         }
 
-        // best value and its first position, per tile
-        if (cnt_cola && ir >= ta.cnt_ir0 && ir < ta.nrows) {
-          const int v = (int)I - (int)(rmin & 0xffffu);
-          if (v > ba.val) {
-            ba.val = v;
+        // this row's best dp per half (I >= A, so the packed subtraction is
+        // exact), kept only for counted rows and columns
+        const uint32_t rowmask2 = (ir >= ta.cnt_ir0 ? 0x0000ffffu : 0u) |
+                                  (ir >= tb.cnt_ir0 ? 0xffff0000u : 0u);
+        const uint32_t d2 = (I2 - rmin) & colmask2 & rowmask2;
+        if (vmax2(d2, best2) != best2) {
+          const uint32_t dlo = d2 & 0xffffu, dhi = d2 >> 16;
+          if (dlo > (best2 & 0xffffu)) {
+            ba.val = (int)dlo;
             ba.row = (int32_t)(ta.wr0 + ir);
-            const uint32_t target = rmin & 0xffffu;
+            const uint32_t target = I - dlo;
             int kk = 0;
 #pragma unroll
             for (int k = P - 1; k >= 0; --k)
               if ((Ap[k] & 0xffffu) == target) kk = k;
             ba.col = (int32_t)(cola + kk);
           }
-        }
-        if (cnt_colb && ir >= tb.cnt_ir0 && ir < tb.nrows) {
-          const int v = (int)I - (int)(rmin >> 16);
-          if (v > bb.val) {
-            bb.val = v;
+          if (dhi > (best2 >> 16)) {
+            bb.val = (int)dhi;
             bb.row = (int32_t)(tb.wr0 + ir);
-            const uint32_t target = rmin >> 16;
+            const uint32_t target = I - dhi;
             int kk = 0;
 #pragma unroll
             for (int k = P - 1; k >= 0; --k)
               if ((Ap[k] >> 16) == target) kk = k;
             bb.col = (int32_t)(colb + kk);
           }
+          best2 = vmax2(d2, best2);
+        }
+        // rows and lane chunks holding a value above the halo: the fix-up box
+        if (vmax2(d2, kHalo2) != kHalo2) {
+          if ((d2 & 0xffffu) > (uint32_t)kHalo) {
+            if (ba.big_r0 == 0x7fffffff) {
+              ba.big_r0 = (int32_t)(ta.wr0 + ir);
+              ba.big_c0 = cola;
+              ba.big_c1 = min(cola + P, ta.n);
+            }
+            ba.big_r1 = (int32_t)(ta.wr0 + ir + 1);
+          }
+          if ((d2 >> 16) > (uint32_t)kHalo) {
+            if (bb.big_r0 == 0x7fffffff) {
+              bb.big_r0 = (int32_t)(tb.wr0 + ir);
+              bb.big_c0 = colb;
+              bb.big_c1 = min(colb + P, tb.n);
+            }
+            bb.big_r1 = (int32_t)(tb.wr0 + ir + 1);
+          }
         }
 
         if constexpr (DPMAP) {
-          if (cnt_cola && ir >= ta.cnt_ir0 && ir < ta.nrows) {
-            int32_t* p = dpa + (ta.wr0 + ir) * lda + cola;
-            if (dpa_al && cola + P <= ta.n && (P % 4) == 0) {
-#pragma unroll
-              for (int k = 0; k < P; k += 4) {
-                int4 v;
-                v.x = (int)I - (int)(Ap[k] & 0xffffu);
-                v.y = (int)I - (int)(Ap[k + 1] & 0xffffu);
-                v.z = (int)I - (int)(Ap[k + 2] & 0xffffu);
-                v.w = (int)I - (int)(Ap[k + 3] & 0xffffu);
-                __stcs(reinterpret_cast<int4*>(p + k), v);
-              }
-            } else {
-#pragma unroll
-              for (int k = 0; k < P; ++k)
-                if (cola + k < ta.n) p[k] = (int)I - (int)(Ap[k] & 0xffffu);
-            }
-          }
-          if (cnt_colb && ir >= tb.cnt_ir0 && ir < tb.nrows) {
-            int32_t* p = dpb + (tb.wr0 + ir) * ldb + colb;
-            if (dpb_al && colb + P <= tb.n && (P % 4) == 0) {
-#pragma unroll
-              for (int k = 0; k < P; k += 4) {
-                int4 v;
-                v.x = (int)I - (int)(Ap[k] >> 16);
-                v.y = (int)I - (int)(Ap[k + 1] >> 16);
-                v.z = (int)I - (int)(Ap[k + 2] >> 16);
-                v.w = (int)I - (int)(Ap[k + 3] >> 16);
-                __stcs(reinterpret_cast<int4*>(p + k), v);
-              }
-            } else {
-#pragma unroll
-              for (int k = 0; k < P; ++k)
-                if (colb + k < tb.n) p[k] = (int)I - (int)(Ap[k] >> 16);
-            }
-          }
+          if ((colmask2 & 0xffffu) && ir >= ta.cnt_ir0 && ir < ta.nrows)
+            store_dp<P, false>(dprow_a + (int64_t)ir * lda, Ap, I, cola, ta.n, dpa_al);
+          if ((colmask2 >> 16) && ir >= tb.cnt_ir0 && ir < tb.nrows)
+            store_dp<P, true>(dprow_b + (int64_t)ir * ldb, Ap, I, colb, tb.n, dpb_al);
         }
       }
     }
@@ -320,32 +389,36 @@ __device__ __forceinline__ void tile_pass_warp(const Job* jobs, int njobs, int64
                               io, ba, bb);
   const unsigned long long ka = tile_key(ba, ga.n);
   const unsigned long long kb = tile_key(bb, gb.n);
+  // the tile's cells above the halo: bounding box over the warp's lanes
+  const int ar0 = __reduce_min_sync(kFull, ba.big_r0), ar1 = __reduce_max_sync(kFull, ba.big_r1);
+  const int br0 = __reduce_min_sync(kFull, bb.big_r0), br1 = __reduce_max_sync(kFull, bb.big_r1);
+  const int ac0 = __reduce_min_sync(kFull, (int)min(ba.big_c0, (int64_t)0x7fffffff));
+  const int ac1 = __reduce_max_sync(kFull, (int)ba.big_c1);
+  const int bc0 = __reduce_min_sync(kFull, (int)min(bb.big_c0, (int64_t)0x7fffffff));
+  const int bc1 = __reduce_max_sync(kFull, (int)bb.big_c1);
   if ((threadIdx.x & 31) == 0) {
-    if (ka) {
-      atomicMax(&A.st->key, ka);
-      if ((int)(ka >> 40) > kHalo) {
-        const int r0 = (int)(ga.wr0 + ga.cnt_ir0);
-        atomicMin(&A.st->box[0], r0);
-        atomicMax(&A.st->box[1], (int)(ga.wr0 + ga.nrows));
-        atomicMin(&A.st->box[2], (int)ga.c0);
-        atomicMax(&A.st->box[3], (int)min(ga.n, ga.wc0 + 32 * P));
-      }
+    if (ka) atomicMax(&A.st->key, ka);
+    if (ar1 >= 0) {
+      atomicMin(&A.st->box[0], ar0);
+      atomicMax(&A.st->box[1], ar1);
+      atomicMin(&A.st->box[2], ac0);
+      atomicMax(&A.st->box[3], ac1);
     }
-    if (jb >= 0 && kb) {
-      atomicMax(&B.st->key, kb);
-      if ((int)(kb >> 40) > kHalo) {
-        const int r0 = (int)(gb.wr0 + gb.cnt_ir0);
-        atomicMin(&B.st->box[0], r0);
-        atomicMax(&B.st->box[1], (int)(gb.wr0 + gb.nrows));
-        atomicMin(&B.st->box[2], (int)gb.c0);
-        atomicMax(&B.st->box[3], (int)min(gb.n, gb.wc0 + 32 * P));
-      }
+    if (jb >= 0 && kb) atomicMax(&B.st->key, kb);
+    if (jb >= 0 && br1 >= 0) {
+      atomicMin(&B.st->box[0], br0);
+      atomicMax(&B.st->box[1], br1);
+      atomicMin(&B.st->box[2], bc0);
+      atomicMax(&B.st->box[3], bc1);
     }
   }
 }
 
+// Size-only tiles fit 128 registers (two 256-thread blocks per SM); the dp-map
+// variant keeps more values live and runs one block per SM.
 template <int P, int FMT, bool DPMAP>
-__global__ void __launch_bounds__(256) k_tiles(const Job* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(256, DPMAP ? 1 : 2) k_tiles(const Job* __restrict__ jobs,
+                                                               int njobs,
                                                int64_t ntiles) {
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   tile_pass_warp<P, FMT, DPMAP>(jobs, njobs, ntiles, w);
@@ -353,15 +426,15 @@ __global__ void __launch_bounds__(256) k_tiles(const Job* __restrict__ jobs, int
 
 // Single matrix: the job travels as a kernel parameter.
 template <int P, int FMT, bool DPMAP>
-__global__ void __launch_bounds__(256) k_tiles_one(const Job job, int64_t ntiles) {
+__global__ void __launch_bounds__(256, DPMAP ? 1 : 2) k_tiles_one(const Job job, int64_t ntiles) {
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   tile_pass_warp<P, FMT, DPMAP>(&job, 1, ntiles, w);
 }
 
 // ---- fix-up and result ------------------------------------------------------
 
-constexpr int kFixWarps = 8;
-constexpr int kFixP = 16;
+constexpr int kFixWarps = 16;
+constexpr int kFixP = 8;            // short per-row chains: the fix-up is latency-bound
 constexpr int kFixW = 32 * kFixP;  // strip width in the fix-up
 
 template <int FMT, bool DPMAP>
@@ -378,7 +451,9 @@ __device__ __forceinline__ void fixup_job(const Job& j) {
   const int rlo = sbox[0], rhi = sbox[1], clo = sbox[2], chi = sbox[3];
   if (rhi > rlo && chi > clo) {
     const int64_t br0 = max(0, rlo - kHalo);
-    const int64_t bc0 = max(0, clo - kHalo);
+    // rounded down to 32 columns: fix-up chunks must stay inside a packed
+    // word and keep vector loads aligned (a wider window is still exact)
+    const int64_t bc0 = (int64_t)(max(0, clo - kHalo) & ~31);
     const int nstrips = (int)((chi - bc0 + kFixW - 1) / kFixW);
     const int rows = (int)(rhi - br0);
     const int warp = threadIdx.x >> 5;

@@ -12,7 +12,7 @@
 // Where its scratch lives: the per-matrix result state, the fix-up progress
 // flags and the fix-up strip carries sit in one file-scope device array,
 // g_noalloc_scratch, sized for matrices of up to kNoAllocMaxRows x
-// kNoAllocMaxCols cells (see the sizes below, about 0.6 MiB).  Every GPU that
+// kNoAllocMaxCols cells (see the sizes below, about 1.1 MiB).  Every GPU that
 // loads this library holds that array until the process exits.  The caller
 // still passes the input matrix and the result buffer.
 //
@@ -160,7 +160,7 @@ extern "C" ms_status ms_max_square_noalloc(const ms_matrix* in, ms_result* out_d
   if (in->m > 0 && in->n > 0) {
     const int64_t W = 32 * j.P;
     j.strips = (int32_t)(in->n <= W ? 1 : 1 + (in->n - W + (W - ms::kHalo) - 1) / (W - ms::kHalo));
-    int64_t br = (in->m * j.strips + 2 * 152 * 8 - 1) / (2 * 152 * 8);
+    int64_t br = (in->m * j.strips + 2 * 152 * 16 - 1) / (2 * 152 * 16);
     br = std::min<int64_t>(std::max<int64_t>((br + 31) / 32 * 32, 32), 4096);
     j.band_rows = (int32_t)std::min<int64_t>(br, in->m);
     j.bands = (int32_t)((in->m + j.band_rows - 1) / j.band_rows);

@@ -104,6 +104,25 @@ def test_squares_on_tile_edges(ctx):
         ctx.set_tuning(band_rows=0)
 
 
+def test_narrow_matrices_with_large_squares(ctx):
+    """Narrow matrices use short lane chunks; squares above the halo at odd
+    columns make the fix-up start at unaligned columns (both formats, alone
+    and batched)."""
+    mats, exps = [], []
+    for i, (m, n) in enumerate([(633, 94), (400, 37), (300, 61), (500, 128), (700, 200),
+                                (260, 33), (900, 255)]):
+        a = gen.bernoulli_u8(m, n, 0.3, seed=900 + i)
+        s = min(m, n) - 3
+        c0 = 1 + (i % 3)
+        a[m - s - 2:m - 2, c0:c0 + s] = 1
+        exp = list(oracle.dp(a, want_map=False)[0]) + [0]
+        assert exp[0] == s
+        run_all_paths(ctx, a, pads=(1,))
+        mats += [to_dev(a), (bits_dev(a, n, pad=1), n)]
+        exps += [exp, exp]
+    assert ctx.batch(mats).cpu().tolist() == exps
+
+
 @pytest.mark.parametrize("shape", [(1, 1), (1, 600), (600, 1), (5, 9), (512, 512), (700, 1500),
                                    (2000, 1300)])
 def test_closed_forms(ctx, shape):
