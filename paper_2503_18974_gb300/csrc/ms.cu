@@ -8,6 +8,7 @@
 #include <new>
 #include <vector>
 
+#include "ms_bits.cuh"
 #include "ms_kernels.cuh"
 
 using ms::Job;
@@ -35,6 +36,18 @@ struct ms_ctx {
   int64_t stage_cap = 0;
   cudaEvent_t stage_free = nullptr;
   bool stage_pending = false;
+
+  // bit-packed search workspace: two level buffers, their block activity maps
+  // and the search state; geometry of the last search (buffers hold zeros
+  // outside the blocks their maps mark active, for that geometry)
+  uint32_t* d_lvl = nullptr;
+  int64_t lvl_cap = 0;  // uint32 words, both buffers
+  uint8_t* d_act = nullptr;
+  int64_t act_cap = 0;
+  ms::bits::State* d_bst = nullptr;
+  int64_t bst_cap = 0;
+  int64_t bits_geom[3] = {-1, -1, -1};  // m, wp, nbw
+  int bits_grid = 0;
 
   // kernel timing (ms_profile_start / ms_profile_stop)
   struct ProfSlot {
@@ -263,6 +276,121 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---- bit-packed size-only search ---------------------------------------------
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D tensor map over `rows` rows of `words` uint32 words, row stride `stride`
+// words, boxes of kSW words x kBR rows, zeros outside.
+bool make_map(CUtensorMap* map, const void* base, int64_t words, int64_t rows, int64_t stride) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)words, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)stride * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)ms::bits::kSW, (cuuint32_t)ms::bits::kBR};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Whether the bitplane search can take this matrix (TMA needs 16-byte
+// aligned rows) and was selected.
+bool bits_search_applies(const ms_ctx* ctx, const ms_matrix* in) {
+  if (in->fmt != MS_BITS32 || ctx->tuning.packed_path != 1) return false;
+  if (in->m <= 0 || in->n <= 0) return false;
+  if ((reinterpret_cast<uintptr_t>(in->data) & 15u) || (in->ld & 3)) return false;
+  return encode_tiled() != nullptr;
+}
+
+ms_status run_bits_search(ms_ctx* ctx, const ms_matrix* in, ms_result* out_dev, cudaStream_t s) {
+  namespace B = ms::bits;
+  const bool cap = capturing(s);
+  const int64_t m = in->m, n = in->n;
+  const int64_t wv = (n + 31) / 32;
+  const int64_t wp = (wv + 3) / 4 * 4;
+  const int nbr = (int)((m + B::kBR - 1) / B::kBR);
+  const int nbw = (int)((wv + B::kBW - 1) / B::kBW);
+  const int64_t nblocks = (int64_t)nbr * nbw;
+  if (nblocks > 0x7fffffff / 2) return MS_ERR_UNSUPPORTED;
+  ms_status st = grow(ctx, ctx->d_lvl, ctx->lvl_cap, 2 * m * wp, cap);
+  if (st != MS_OK) return st;
+  st = grow(ctx, ctx->d_act, ctx->act_cap, 2 * nblocks, cap);
+  if (st != MS_OK) return st;
+  st = grow(ctx, ctx->d_bst, ctx->bst_cap, 1, cap);
+  if (st != MS_OK) return st;
+  if (ctx->bits_geom[0] != m || ctx->bits_geom[1] != wp || ctx->bits_geom[2] != nbw) {
+    if (cap) return MS_ERR_UNSUPPORTED;
+    if (cudaMemsetAsync(ctx->d_lvl, 0, (size_t)(2 * m * wp) * 4, s) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_act, 0, (size_t)(2 * nblocks), s) != cudaSuccess)
+      return MS_ERR_CUDA;
+    ctx->bits_geom[0] = m;
+    ctx->bits_geom[1] = wp;
+    ctx->bits_geom[2] = nbw;
+  }
+  if (ctx->bits_grid == 0) {
+    if (cudaFuncSetAttribute(B::k_bits_search, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)B::kSmemBytes) != cudaSuccess)
+      return MS_ERR_CUDA;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, B::k_bits_search, B::kThreads,
+                                                      B::kSmemBytes) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess ||
+        per_sm < 1)
+      return MS_ERR_CUDA;
+    ctx->bits_grid = per_sm * sms;
+  }
+  CUtensorMap maps[3];
+  uint32_t* bx = ctx->d_lvl;
+  uint32_t* by = ctx->d_lvl + m * wp;
+  if (!make_map(&maps[0], in->data, wv, m, in->ld) || !make_map(&maps[1], bx, wv, m, wp) ||
+      !make_map(&maps[2], by, wv, m, wp))
+    return MS_ERR_CUDA;
+  B::Args args;
+  args.m = m;
+  args.n = n;
+  args.wv = wv;
+  args.wp = wp;
+  args.buf[0] = nullptr;
+  args.buf[1] = bx;
+  args.buf[2] = by;
+  args.act[0] = nullptr;
+  args.act[1] = ctx->d_act;
+  args.act[2] = ctx->d_act + nblocks;
+  args.nbr = nbr;
+  args.nbw = nbw;
+  args.st = ctx->d_bst;
+  args.out = out_dev;
+  const int grid = (int)std::min<int64_t>(ctx->bits_grid, std::max<int64_t>(nblocks, 1));
+  ProfScope ps(ctx, s, kProfOther);
+  B::k_bits_reset<<<1, B::kMaxPasses, 0, s>>>(ctx->d_bst);
+  void* kargs[] = {&maps[0], &maps[1], &maps[2], &args};
+  if (cudaLaunchCooperativeKernel((const void*)B::k_bits_search, dim3(grid), dim3(B::kThreads),
+                                  kargs, B::kSmemBytes, s) != cudaSuccess)
+    return MS_ERR_CUDA;
+  return cuda_status(cudaGetLastError());
+}
+
 ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_dp,
                      ms_result* out_dev, cudaStream_t s) {
   ms_status st = check_matrix(in);
@@ -272,6 +400,7 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
     if (in->m > 0 && in->n > 0 && ld_dp < in->n) return MS_ERR_INVALID;
   }
   DeviceGuard g(ctx->device);
+  if (!dp && bits_search_applies(ctx, in)) return run_bits_search(ctx, in, out_dev, s);
   Job j = plan_job(ctx, in);
   st = ensure_workspace(ctx, 1, j.m * (int64_t)j.strips_fix, j.strips_fix, s);
   if (st != MS_OK) return st;
@@ -375,6 +504,9 @@ ms_status ms_destroy(ms_ctx* ctx) {
     release(ctx, ctx->d_carry, ctx->carry_cap);
     release(ctx, ctx->d_progress, ctx->progress_cap);
     release(ctx, ctx->d_jobs, ctx->jobs_cap);
+    release(ctx, ctx->d_lvl, ctx->lvl_cap);
+    release(ctx, ctx->d_act, ctx->act_cap);
+    release(ctx, ctx->d_bst, ctx->bst_cap);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
     for (auto& ps : ctx->prof_pool) {
@@ -389,6 +521,7 @@ ms_status ms_destroy(ms_ctx* ctx) {
 ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t) {
   if (!ctx || !t) return MS_ERR_INVALID;
   if (t->band_rows < 0 || t->band_rows > 65000) return MS_ERR_INVALID;
+  if (t->packed_path < 0 || t->packed_path > 1) return MS_ERR_INVALID;
   ctx->tuning = *t;
   return MS_OK;
 }

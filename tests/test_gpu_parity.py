@@ -244,3 +244,51 @@ def test_invalid_arguments(ctx, ms):
     assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), x.data_ptr(), None) == 6
     desc = ms.describe(x)
     assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), None, None) == 1
+
+
+@pytest.fixture
+def packed_ctx(ctx):
+    ctx.set_tuning(packed_path=1)
+    yield ctx
+    ctx.set_tuning(packed_path=0)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 40), (40, 1), (31, 33), (64, 1024), (100, 1025),
+                                   (257, 3000), (1000, 700), (33, 2050)])
+@pytest.mark.parametrize("p", [0.2, 0.7, 0.95])
+def test_packed_search_random(packed_ctx, shape, p):
+    """The bitplane doubling / binary search (packed size-only path)."""
+    m, n = shape
+    a = gen.bernoulli_u8(m, n, p, seed=7 * m + n + int(100 * p))
+    (K, r, c), _ = oracle.dp(a, want_map=False)
+    for pad in (0, 1):
+        w = gen.pack_bits(a, n, ldw=((n + 31) // 32 + 3) // 4 * 4, pad_value=pad)
+        x = torch.from_numpy(w.view(np.int32)).to(DEV)
+        assert packed_ctx.max_square(x, n=n).cpu().tolist() == [K, r, c, 0], (shape, p, pad)
+
+
+def test_packed_search_planted_and_closed_forms(packed_ctx):
+    rng = np.random.default_rng(21)
+    cases = []
+    for t in range(8):
+        m, n = int(rng.integers(50, 1500)), int(rng.integers(50, 2500))
+        a = gen.bernoulli_u8(m, n, 0.8, seed=300 + t)
+        s = int(rng.integers(20, min(m, n) + 1))
+        r0, c0 = int(rng.integers(0, m - s + 1)), int(rng.integers(0, n - s + 1))
+        a[r0:r0 + s, c0:c0 + s] = 1
+        cases.append(a)
+    cases += [np.ones((300, 500), np.uint8), np.ones((777, 64), np.uint8),
+              np.zeros((200, 300), np.uint8)]
+    one = np.zeros((90, 3000), np.uint8)
+    one[55, 2047] = 1
+    cases.append(one)
+    for a in cases:
+        m, n = a.shape
+        (K, r, c), _ = oracle.dp(a, want_map=False)
+        w = gen.pack_bits(a, n, ldw=((n + 31) // 32 + 3) // 4 * 4, pad_value=1)
+        x = torch.from_numpy(w.view(np.int32)).to(DEV)
+        assert packed_ctx.max_square(x, n=n).cpu().tolist() == [K, r, c, 0], (m, n)
+        # the same matrix through the tile path
+        packed_ctx.set_tuning(packed_path=0)
+        assert packed_ctx.max_square(x, n=n).cpu().tolist() == [K, r, c, 0], (m, n)
+        packed_ctx.set_tuning(packed_path=1)
