@@ -18,7 +18,8 @@ Workloads (sizes from the configurations this benchmark mirrors):
   c3-u8 / c3-u8-dp / c3-bits / c3-bits-dp
            32768 x 32768, p = 0.9, one planted 600-square, seed 3
   c3q-*    the same with 8192 rows (for profiler captures)
-  c4       4096 uint8 matrices, m and n log-uniform in [16, 2048], one ms_batch
+  c4       4096 uint8 matrices, m and n log-uniform in [16, 2048]: one autotuned
+           ms_batch per step replayed from a CUDA graph (plain calls reported beside)
 """
 from __future__ import annotations
 
@@ -148,17 +149,42 @@ class PlainSet(Workload):
         self.bytes_per_cell = (1.0 if fmt == 0 else 0.125) + (4.0 if dpmap else 0.0)
         self.dev_bufs = None
 
-    def step(self, ctx, stream=None, tensors=None):
+    def prepare(self, ms, ctx, tensors=None):
+        """ctypes descriptors for every matrix (the C ABI is called directly)."""
+        import ctypes
+        descs = []
         for i, mt in enumerate(self.mats):
             x, n, fmt = mt.args(None if tensors is None else tensors[i])
-            if self.dpmap:
-                ctx.dp_map(x, n=n, fmt=fmt, dp=self.dps[i], out=self.res[i], stream=stream)
-            else:
-                ctx.max_square(x, n=n, fmt=fmt, out=self.res[i], stream=stream)
+            descs.append(ms.describe(x, n, fmt))
+        arr = (ms._Matrix * len(descs))(*descs)
+        base = ctypes.addressof(arr)
+        ptrs = [ctypes.cast(base + i * ctypes.sizeof(ms._Matrix), ctypes.POINTER(ms._Matrix))
+                for i in range(len(descs))]
+        res = [self.res[i].data_ptr() for i in range(len(descs))]
+        dps = [(d.data_ptr(), d.stride(0)) for d in self.dps] if self.dpmap else None
+        return arr, ptrs, res, dps
 
-    def batch_step(self, ctx, stream=None):
-        ctx.batch([mt.args()[:2] if mt.fmt else mt.args()[0] for mt in self.mats],
-                  out=self.res, stream=stream)
+    def step(self, ms, ctx, prep, stream_ptr):
+        """One plain call per matrix."""
+        arr, ptrs, res, dps = prep
+        L, h = ms.lib(), ctx._h
+        if self.dpmap:
+            for i in range(len(ptrs)):
+                rc = L.ms_dp_map(h, ptrs[i], dps[i][0], dps[i][1], res[i], stream_ptr)
+                if rc:
+                    raise ms.MSError(rc, "ms_dp_map")
+        else:
+            for i in range(len(ptrs)):
+                rc = L.ms_max_square(h, ptrs[i], res[i], stream_ptr)
+                if rc:
+                    raise ms.MSError(rc, "ms_max_square")
+
+    def batch_step(self, ms, ctx, prep, stream_ptr):
+        """One ms_batch call over all matrices."""
+        arr = prep[0]
+        rc = ms.lib().ms_batch(ctx._h, arr, len(self.mats), self.res.data_ptr(), stream_ptr)
+        if rc:
+            raise ms.MSError(rc, "ms_batch")
 
     def h2d_bytes(self):
         return sum(mt.nbytes for mt in self.mats)
@@ -421,6 +447,18 @@ def run_reference(args, world, rank, local, pg):
     print(json.dumps(line), flush=True)
 
 
+def timed(fn, steps, stream):
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(steps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
 def run_ours(args, world, rank, local, pg):
     import torch
 
@@ -436,49 +474,70 @@ def run_ours(args, world, rank, local, pg):
     wl = make_workload(args.workload, device, host=True)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream or None
+    prep = wl.prepare(ms, ctx)
+    batch_headline = args.workload == "c4"
+    multi = len(wl.mats) > 1 and not wl.dpmap
 
-    # warm-up (also sizes the workspace)
+    # the batched form: autotuned, then captured in a CUDA graph
+    graph = None
+    tuned = None
+    if multi:
+        tuned = ctx.autotune([mt.args()[:2] if mt.fmt else mt.args()[0] for mt in wl.mats])
+        wl.batch_step(ms, ctx, prep, sp)  # uploads the job table outside the capture
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph, stream=side):
+                wl.batch_step(ms, ctx, prep, side.cuda_stream)
+        torch.cuda.synchronize()
+
+    def plain():
+        wl.step(ms, ctx, prep, sp)
+
+    def batched():
+        graph.replay()
+
+    headline = batched if batch_headline else plain
+
     for _ in range(args.warmup):
-        wl.step(ctx)
+        headline()
     torch.cuda.synchronize()
 
-    # timed region: K steps, device-timed
+    # timed region: K steps, device-timed, clocks sampled
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.4)
     barrier(pg)
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_wall0 = time.time()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        wl.step(ctx)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    ms_total = timed(headline, args.steps, stream)
     t_wall1 = time.time()
     barrier(pg)
     sampler.mark(t_wall0, t_wall1)
     clocks = sampler.stop()
-    ms_total = max_over_ranks(pg, ev0.elapsed_time(ev1), device)
+    ms_total = max_over_ranks(pg, ms_total, device)
     ms_step = ms_total / args.steps
     value = world * wl.cells * args.steps / (ms_total * 1e-3) / 1e9
 
-    # dominant kernel (tile pass): the same K steps again with a CUDA event pair
-    # recorded by the library around every launch on this stream; achieved =
-    # algorithmic bytes / summed tile-kernel time
+    # dominant kernel: the same K steps again with a CUDA event pair recorded
+    # by the library around every launch on this stream
     ctx.profile_start()
     for _ in range(args.steps):
-        wl.step(ctx)
+        if batch_headline:
+            wl.batch_step(ms, ctx, prep, sp)
+        else:
+            plain()
     prof = ctx.profile_stop()
     peak, peak_kind = measured_peaks()
     roof = None
-    # the dominant kernel: the tile pass, or the bitplane search on packed input
     if prof.other_ms > prof.tile_ms:
         kern_ms, kern_launches, kern_name = prof.other_ms, prof.other_launches, \
             "k_bits_search (bitplane doubling + binary search)"
     else:
         kern_ms, kern_launches, kern_name = prof.tile_ms, prof.tile_launches, \
-            "k_tiles_one (tile pass)"
+            ("k_batch_tiles (persistent tile queue)" if batch_headline
+             else "k_tiles_one (tile pass)")
     if kern_launches and kern_ms > 0:
         alg_bytes = wl.cells * wl.bytes_per_cell * args.steps
         achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
@@ -495,49 +554,51 @@ def run_ours(args, world, rank, local, pg):
                 "fixup_ms_per_step": prof.fixup_ms / args.steps,
                 "search_ms_per_step": prof.other_ms / args.steps,
                 "how": "per-launch CUDA events on the launching stream, same K steps re-run"}
-    launches = (prof.tile_launches + prof.fixup_launches + prof.other_launches)
+    launches_per_step = (prof.tile_launches + prof.fixup_launches + prof.other_launches) \
+        / args.steps
+    if batch_headline:
+        launches_per_step += 0  # the graph replays the same launches (queue reset is a memset)
+    launches = int(round(launches_per_step * args.steps))
 
-    # batched form of the same workload (one ms_batch per step)
-    batched = None
-    if len(wl.mats) > 1 and not wl.dpmap:
+    # batched vs plain, same matrices
+    compare = None
+    if multi:
+        other = plain if batch_headline else batched
         for _ in range(2):
-            wl.batch_step(ctx)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        for _ in range(args.steps):
-            wl.batch_step(ctx)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        bms = ev0.elapsed_time(ev1) / args.steps
-        batched = {"value": wl.cells / (bms * 1e-3) / 1e9, "unit": "Gcells/s", "ms_per_step": bms,
-                   "how": "one ms_batch call per step over the same matrices"}
+            other()
+        oms = timed(other, args.steps, stream) / args.steps
+        compare = {"plain" if batch_headline else "batched_graph": {
+            "value": wl.cells / (oms * 1e-3) / 1e9, "unit": "Gcells/s", "ms_per_step": oms,
+            "how": ("one ms_max_square call per matrix, eager launches" if batch_headline else
+                    "one ms_batch per step (autotuned, persistent tile queue), graph replay")},
+            "autotuned": tuned}
 
-    # e2e: inputs in pinned host memory, copies and result read-back timed
+    # e2e: pinned host inputs copied to fixed device buffers, the public call
+    # (ms_max_square per matrix, or ms_batch), results read back, per step
     bufs = [torch.empty_like(mt.dev) for mt in wl.mats]
+    eprep = wl.prepare(ms, ctx, tensors=bufs)
     res_host = torch.empty(wl.res.shape, dtype=torch.int32, pin_memory=True)
-    for _ in range(max(1, args.warmup)):
+
+    def e2e_step():
         for b, mt in zip(bufs, wl.mats):
             b.copy_(mt.host, non_blocking=True)
-        wl.step(ctx, tensors=bufs)
-        res_host.copy_(wl.res, non_blocking=True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        for b, mt in zip(bufs, wl.mats):
-            b.copy_(mt.host, non_blocking=True)
-        wl.step(ctx, tensors=bufs)
+        if batch_headline:
+            wl.batch_step(ms, ctx, eprep, sp)
+        else:
+            wl.step(ms, ctx, eprep, sp)
         res_host.copy_(wl.res, non_blocking=True)
         torch.cuda.synchronize()
-    ev1.record(stream)
-    torch.cuda.synchronize()
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
     e2e_ms = max_over_ranks(pg, (time.perf_counter() - t0) * 1e3, device)
     e2e = {"value": world * wl.cells * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "Gcells/s",
            "h2d_bytes_per_step": wl.h2d_bytes(), "d2h_bytes_per_step": res_host.numel() * 4,
-           "how": "pinned host inputs copied H2D, ms_* call, results read back, per step"}
+           "how": "pinned host inputs copied H2D, the public ms_* call, results read back"}
 
-    # correctness spot check of the timed results against nothing stored:
-    # statuses must be MS_OK
     ok = bool((wl.res[:, 3] == 0).all().item())
 
     cpu = None
@@ -545,15 +606,16 @@ def run_ours(args, world, rank, local, pg):
         cpu = cpu_baseline(wl.specs)
 
     if rank == 0:
-        pk = None
         line = {"metric": METRIC, "value": value, "unit": "Gcells/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": pk,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": wl.dtype, "data": "synthetic (seeded SplitMix64 Bernoulli matrices)",
                 "config": {**wl.config(), "parallelism": f"replicas x{world}",
-                           "packed_path": packed_path},
+                           "packed_path": packed_path,
+                           "timed_path": ("ms_batch, CUDA graph replay" if batch_headline
+                                          else "one ms_* call per matrix (plain)")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks, "batched": batched,
+                "gpu_launches": launches, "clocks": clocks, "compare": compare,
                 "status_ok": ok}
         print(json.dumps(line), flush=True)
     ctx.close()

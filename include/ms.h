@@ -147,6 +147,20 @@ typedef struct {
 ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t);
 ms_status ms_get_tuning(ms_ctx* ctx, ms_tuning* t);
 
+/* Autotuner (a library feature; the paper has no counterpart).  Times the
+ * work of ms_max_square (count == 1) or ms_batch (count > 1) on the given
+ * matrices for each candidate tuning -- band heights 32..1024 and the
+ * automatic choice, and for MS_BITS32 size-only work both packed paths --
+ * keeps the fastest, and caches it in the context under the workload's class
+ * (entry point, format mix, log2 of the cell count, log2 of the matrix
+ * count).  Later calls of that class with ms_tuning.band_rows == 0 use the
+ * cached choice.  `outs_dev` receives results (count entries) and is
+ * scratch.  Blocks the calling thread until the timing runs finish; must
+ * not be called during stream capture.  The chosen tuning is written to
+ * `chosen` if non-null. */
+ms_status ms_autotune(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_result* outs_dev,
+                      ms_stream_t s, ms_tuning* chosen);
+
 /* ---- kernel timing --------------------------------------------------------
  * Between ms_profile_start and ms_profile_stop the context records a CUDA
  * event pair around every kernel it launches (on the caller's stream, so the

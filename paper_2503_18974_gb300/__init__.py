@@ -73,7 +73,7 @@ _lib = None
 
 EXPORTS = ("ms_create", "ms_destroy", "ms_max_square", "ms_dp_map", "ms_batch",
            "ms_status_string", "ms_set_tuning", "ms_get_tuning", "ms_profile_start",
-           "ms_profile_stop")
+           "ms_profile_stop", "ms_autotune", "ms_max_square_noalloc")
 
 
 def lib():
@@ -100,6 +100,9 @@ def lib():
         L.ms_set_tuning.argtypes = [vp, ctypes.POINTER(_Tuning)]
         L.ms_get_tuning.restype = ctypes.c_int
         L.ms_get_tuning.argtypes = [vp, ctypes.POINTER(_Tuning)]
+        L.ms_autotune.restype = ctypes.c_int
+        L.ms_autotune.argtypes = [vp, ctypes.POINTER(_Matrix), ctypes.c_int32, vp, vp,
+                                  ctypes.POINTER(_Tuning)]
         L.ms_profile_start.restype = ctypes.c_int
         L.ms_profile_start.argtypes = [vp, ctypes.c_int32]
         L.ms_profile_stop.restype = ctypes.c_int
@@ -171,6 +174,21 @@ class MaxSquare:
         p = Profile()
         _check(lib().ms_profile_stop(self._h, ctypes.byref(p)), "ms_profile_stop")
         return p
+
+    def autotune(self, mats: Sequence, stream=None) -> dict:
+        """Time candidate tunings on these matrices (one: the ms_max_square path;
+        several: ms_batch) and cache the fastest for their workload class."""
+        import torch
+        descs = (_Matrix * len(mats))()
+        dev = None
+        for i, item in enumerate(mats):
+            descs[i] = describe(*item) if isinstance(item, tuple) else describe(item)
+            dev = (item[0] if isinstance(item, tuple) else item).device
+        out = torch.empty((len(mats), 4), dtype=torch.int32, device=dev)
+        t = _Tuning()
+        _check(lib().ms_autotune(self._h, descs, len(mats), out.data_ptr(), _stream_ptr(stream),
+                                 ctypes.byref(t)), "ms_autotune")
+        return {"band_rows": t.band_rows, "packed_path": t.packed_path}
 
     def get_tuning(self) -> dict:
         t = _Tuning()

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -29,11 +30,12 @@ struct ms_ctx {
 
   // batch job table: device copy, the host image it was uploaded from, and a
   // pinned staging buffer guarded by an event
-  Job* d_jobs = nullptr;
-  int64_t jobs_cap = 0;
-  std::vector<Job> uploaded;
-  Job* h_stage = nullptr;
+  unsigned char* d_table = nullptr;  // [jobs | tasks | queue counter]
+  int64_t table_cap = 0;             // bytes
+  std::vector<unsigned char> uploaded;
+  unsigned char* h_stage = nullptr;
   int64_t stage_cap = 0;
+  int batch_grid = 0;
   cudaEvent_t stage_free = nullptr;
   bool stage_pending = false;
 
@@ -48,6 +50,9 @@ struct ms_ctx {
   int64_t bst_cap = 0;
   int64_t bits_geom[3] = {-1, -1, -1};  // m, wp, nbw
   int bits_grid = 0;
+
+  // autotuned choices by workload class (see ms_autotune)
+  std::map<uint64_t, ms_tuning> tuned;
 
   // kernel timing (ms_profile_start / ms_profile_stop)
   struct ProfSlot {
@@ -148,6 +153,30 @@ int auto_band_rows(int64_t m, int64_t strips) {
   return (int)std::min<int64_t>(auto_band_rows_for(m * strips), std::max<int64_t>(m, 1));
 }
 
+// Workload class for the autotune cache: entry point (single / batch),
+// format mix, log2 of the total cell count and of the matrix count.
+uint64_t tune_class(const ms_matrix* ins, int64_t count, bool batch) {
+  int64_t cells = 0;
+  int fmts = 0;
+  for (int64_t i = 0; i < count; ++i) {
+    cells += ins[i].m * ins[i].n;
+    fmts |= 1 << (ins[i].fmt & 1);
+  }
+  int lc = 0, lk = 0;
+  while ((1ll << lc) < cells && lc < 62) ++lc;
+  while ((1ll << lk) < count && lk < 62) ++lk;
+  return ((uint64_t)(batch ? 1 : 0) << 60) | ((uint64_t)fmts << 56) | ((uint64_t)lc << 8) |
+         (uint64_t)lk;
+}
+
+// The tuning a call uses: explicit band_rows from ms_set_tuning wins, else a
+// cached autotune result for the class, else the context's tuning (automatic).
+ms_tuning effective_tuning(const ms_ctx* ctx, const ms_matrix* ins, int64_t count, bool batch) {
+  if (ctx->tuning.band_rows > 0 || ctx->tuned.empty()) return ctx->tuning;
+  auto it = ctx->tuned.find(tune_class(ins, count, batch));
+  return it == ctx->tuned.end() ? ctx->tuning : it->second;
+}
+
 ms_status check_matrix(const ms_matrix* in) {
   if (!in) return MS_ERR_INVALID;
   if (in->m < 0 || in->n < 0) return MS_ERR_INVALID;
@@ -164,7 +193,7 @@ ms_status check_matrix(const ms_matrix* in) {
   return MS_OK;
 }
 
-Job plan_job(const ms_ctx* ctx, const ms_matrix* in) {
+Job plan_job(const ms_tuning& tune, const ms_matrix* in) {
   Job j;
   std::memset(&j, 0, sizeof(j));
   j.data = in->data;
@@ -175,9 +204,8 @@ Job plan_job(const ms_ctx* ctx, const ms_matrix* in) {
   j.P = choose_P(in->n);
   if (in->m > 0 && in->n > 0) {
     j.strips = (int32_t)strips_for(in->n, j.P);
-    j.band_rows = ctx->tuning.band_rows > 0 ? (int32_t)std::min<int64_t>(ctx->tuning.band_rows,
-                                                                          in->m)
-                                            : auto_band_rows(in->m, j.strips);
+    j.band_rows = tune.band_rows > 0 ? (int32_t)std::min<int64_t>(tune.band_rows, in->m)
+                                     : auto_band_rows(in->m, j.strips);
     j.bands = (int32_t)((in->m + j.band_rows - 1) / j.band_rows);
   }
   j.aligned = (in->fmt == MS_U8) && (reinterpret_cast<uintptr_t>(in->data) % 16 == 0) &&
@@ -316,8 +344,8 @@ bool make_map(CUtensorMap* map, const void* base, int64_t words, int64_t rows, i
 
 // Whether the bitplane search can take this matrix (TMA needs 16-byte
 // aligned rows) and was selected.
-bool bits_search_applies(const ms_ctx* ctx, const ms_matrix* in) {
-  if (in->fmt != MS_BITS32 || ctx->tuning.packed_path != 1) return false;
+bool bits_search_applies(const ms_tuning& tune, const ms_matrix* in) {
+  if (in->fmt != MS_BITS32 || tune.packed_path != 1) return false;
   if (in->m <= 0 || in->n <= 0) return false;
   if ((reinterpret_cast<uintptr_t>(in->data) & 15u) || (in->ld & 3)) return false;
   return encode_tiled() != nullptr;
@@ -400,8 +428,9 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
     if (in->m > 0 && in->n > 0 && ld_dp < in->n) return MS_ERR_INVALID;
   }
   DeviceGuard g(ctx->device);
-  if (!dp && bits_search_applies(ctx, in)) return run_bits_search(ctx, in, out_dev, s);
-  Job j = plan_job(ctx, in);
+  const ms_tuning tune = effective_tuning(ctx, in, 1, false);
+  if (!dp && bits_search_applies(tune, in)) return run_bits_search(ctx, in, out_dev, s);
+  Job j = plan_job(tune, in);
   st = ensure_workspace(ctx, 1, j.m * (int64_t)j.strips_fix, j.strips_fix, s);
   if (st != MS_OK) return st;
   j.tile0 = 0;
@@ -421,22 +450,6 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   return cuda_status(e);
 }
 
-template <int FMT>
-cudaError_t launch_group(const Job* d_jobs, int njobs, int64_t ntiles, int P, cudaStream_t s) {
-  if (ntiles <= 0) return cudaSuccess;
-  const int64_t warps = (ntiles + 1) / 2;
-  const int wpb = kTileThreads / 32;
-  const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
-  switch (P) {
-    case 1: ms::k_tiles<1, FMT, false><<<grid, kTileThreads, 0, s>>>(d_jobs, njobs, ntiles); break;
-    case 2: ms::k_tiles<2, FMT, false><<<grid, kTileThreads, 0, s>>>(d_jobs, njobs, ntiles); break;
-    case 4: ms::k_tiles<4, FMT, false><<<grid, kTileThreads, 0, s>>>(d_jobs, njobs, ntiles); break;
-    case 8: ms::k_tiles<8, FMT, false><<<grid, kTileThreads, 0, s>>>(d_jobs, njobs, ntiles); break;
-    default: ms::k_tiles<16, FMT, false><<<grid, kTileThreads, 0, s>>>(d_jobs, njobs, ntiles); break;
-  }
-  return cudaGetLastError();
-}
-
 __global__ void k_fixup_mixed(const Job* __restrict__ jobs, int njobs) {
   const int j = blockIdx.x;
   if (j >= njobs) return;
@@ -447,8 +460,12 @@ __global__ void k_fixup_mixed(const Job* __restrict__ jobs, int njobs) {
     ms::fixup_job<MS_BITS32, false>(job);
 }
 
-bool same_jobs(const std::vector<Job>& a, const Job* b, int64_t n) {
-  return (int64_t)a.size() == n && std::memcmp(a.data(), b, (size_t)n * sizeof(Job)) == 0;
+// Steps a warp spends on tile t of job j (window rows + lane skew).
+int tile_steps(const Job& j, int64_t t) {
+  const int64_t band = t / j.strips;
+  const int64_t r0 = band * j.band_rows;
+  const int64_t r1 = std::min<int64_t>(j.m, r0 + j.band_rows);
+  return (int)(r1 - (band == 0 ? 0 : r0 - ms::kHalo)) + 31;
 }
 
 }  // namespace
@@ -503,7 +520,7 @@ ms_status ms_destroy(ms_ctx* ctx) {
     release(ctx, ctx->d_states, ctx->states_cap);
     release(ctx, ctx->d_carry, ctx->carry_cap);
     release(ctx, ctx->d_progress, ctx->progress_cap);
-    release(ctx, ctx->d_jobs, ctx->jobs_cap);
+    release(ctx, ctx->d_table, ctx->table_cap);
     release(ctx, ctx->d_lvl, ctx->lvl_cap);
     release(ctx, ctx->d_act, ctx->act_cap);
     release(ctx, ctx->d_bst, ctx->bst_cap);
@@ -558,16 +575,17 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   const bool cap = capturing(s);
 
   // plan: group tiles by (format, columns per lane) so each group is one launch
+  const ms_tuning tune = effective_tuning(ctx, ins_host, count, true);
   std::vector<Job> jobs((size_t)count);
   int64_t carry = 0, progress = 0, work = 0;
   for (int32_t i = 0; i < count; ++i) {
-    jobs[i] = plan_job(ctx, &ins_host[i]);
+    jobs[i] = plan_job(tune, &ins_host[i]);
     carry += jobs[i].m * (int64_t)jobs[i].strips_fix;
     progress += jobs[i].strips_fix;
     work += jobs[i].m * (int64_t)jobs[i].strips;
   }
   // one band height for the whole batch, sized on the batch's total work
-  const int64_t br = ctx->tuning.band_rows > 0 ? ctx->tuning.band_rows : auto_band_rows_for(work);
+  const int64_t br = tune.band_rows > 0 ? tune.band_rows : auto_band_rows_for(work);
   for (Job& j : jobs) {
     if (j.m > 0 && j.n > 0) {
       j.band_rows = (int32_t)std::min<int64_t>(br, j.m);
@@ -576,73 +594,171 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   }
   ms_status st = ensure_workspace(ctx, count, carry, progress, s);
   if (st != MS_OK) return st;
-  std::vector<int32_t> order((size_t)count);
-  for (int32_t i = 0; i < count; ++i) order[i] = i;
-  auto group_of = [&](const Job& j) { return j.fmt * 8 + __builtin_ctz((unsigned)j.P); };
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return group_of(jobs[a]) < group_of(jobs[b]);
-  });
-  std::vector<Job> table((size_t)count);
+  // tiles of one format and lane width pair up in a warp; pairs of similar
+  // length, longest first, form the queue of the persistent launch
+  struct TileRef { int32_t job, tile, steps; };
+  std::vector<std::vector<TileRef>> groups(2 * 32);
   int64_t carry_off = 0, prog_off = 0;
-  struct Group { int fmt, P, first, count; int64_t ntiles; };
-  std::vector<Group> groups;
-  for (int32_t r = 0; r < count; ++r) {
-    const int32_t i = order[r];
-    Job j = jobs[i];
-    const int gid = group_of(j);
-    if (groups.empty() || group_of(table[groups.back().first]) != gid)
-      groups.push_back(Group{j.fmt, j.P, r, 0, 0});
-    Group& gr = groups.back();
-    j.tile0 = gr.ntiles;
-    gr.ntiles += tiles_of(j);
-    gr.count++;
+  for (int32_t i = 0; i < count; ++i) {
+    Job& j = jobs[i];
+    j.tile0 = 0;
     j.out = outs_dev + i;
-    j.st = ctx->d_states + r;
+    j.st = ctx->d_states + i;
     j.carry = ctx->d_carry + carry_off;
     j.progress = ctx->d_progress + prog_off;
     carry_off += j.m * (int64_t)j.strips_fix;
     prog_off += j.strips_fix;
-    table[r] = j;
+    const int64_t nt = tiles_of(j);
+    auto& g = groups[j.fmt * 32 + j.P];
+    for (int64_t t = 0; t < nt; ++t) g.push_back(TileRef{i, (int32_t)t, tile_steps(j, t)});
   }
+  std::vector<ms::PairTask> tasks;
+  std::vector<int> task_steps;
+  for (auto& g : groups) {
+    std::stable_sort(g.begin(), g.end(),
+                     [](const TileRef& a, const TileRef& b) { return a.steps > b.steps; });
+    for (size_t k = 0; k < g.size(); k += 2) {
+      ms::PairTask t;
+      t.job_a = g[k].job;
+      t.tile_a = g[k].tile;
+      t.job_b = k + 1 < g.size() ? g[k + 1].job : -1;
+      t.tile_b = k + 1 < g.size() ? g[k + 1].tile : 0;
+      tasks.push_back(t);
+      task_steps.push_back(g[k].steps);
+    }
+  }
+  {
+    std::vector<size_t> idx(tasks.size());
+    for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](size_t a, size_t b) { return task_steps[a] > task_steps[b]; });
+    std::vector<ms::PairTask> sorted(tasks.size());
+    for (size_t k = 0; k < idx.size(); ++k) sorted[k] = tasks[idx[k]];
+    tasks.swap(sorted);
+  }
+  const int ntasks = (int)tasks.size();
 
-  // job table upload (skipped when identical to the table already on the device)
-  if (!same_jobs(ctx->uploaded, table.data(), count)) {
+  // table image: [jobs | tasks | queue counter], 16-byte aligned sections
+  const size_t jobs_bytes = ((size_t)count * sizeof(Job) + 15) / 16 * 16;
+  const size_t tasks_bytes = ((size_t)ntasks * sizeof(ms::PairTask) + 15) / 16 * 16;
+  const size_t table_bytes = jobs_bytes + tasks_bytes + 16;
+  std::vector<unsigned char> image(table_bytes, 0);
+  std::memcpy(image.data(), jobs.data(), (size_t)count * sizeof(Job));
+  if (ntasks) std::memcpy(image.data() + jobs_bytes, tasks.data(), (size_t)ntasks * sizeof(ms::PairTask));
+
+  // upload only when it differs from the table already on the device
+  if (ctx->uploaded != image) {
     if (cap) return MS_ERR_UNSUPPORTED;  // first run the call once outside capture
-    st = grow(ctx, ctx->d_jobs, ctx->jobs_cap, count, false);
+    st = grow(ctx, ctx->d_table, ctx->table_cap, (int64_t)table_bytes, false);
     if (st != MS_OK) return st;
     if (ctx->stage_pending) cudaEventSynchronize(ctx->stage_free);
-    if (ctx->stage_cap < count) {
+    if (ctx->stage_cap < (int64_t)table_bytes) {
       if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
       ctx->h_stage = nullptr;
       ctx->stage_cap = 0;
-      if (cudaMallocHost(&ctx->h_stage, (size_t)count * sizeof(Job)) != cudaSuccess) {
+      if (cudaMallocHost(&ctx->h_stage, table_bytes) != cudaSuccess) {
         cudaGetLastError();
         return MS_ERR_OOM;
       }
-      ctx->stage_cap = count;
+      ctx->stage_cap = (int64_t)table_bytes;
     }
-    std::memcpy(ctx->h_stage, table.data(), (size_t)count * sizeof(Job));
-    if (cudaMemcpyAsync(ctx->d_jobs, ctx->h_stage, (size_t)count * sizeof(Job),
-                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+    std::memcpy(ctx->h_stage, image.data(), table_bytes);
+    if (cudaMemcpyAsync(ctx->d_table, ctx->h_stage, table_bytes, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
       return MS_ERR_CUDA;
     cudaEventRecord(ctx->stage_free, s);
     ctx->stage_pending = true;
-    ctx->uploaded = table;
+    ctx->uploaded.swap(image);
   }
+  const Job* d_jobs = reinterpret_cast<const Job*>(ctx->d_table);
+  const ms::PairTask* d_tasks = reinterpret_cast<const ms::PairTask*>(ctx->d_table + jobs_bytes);
+  int* d_queue = reinterpret_cast<int*>(ctx->d_table + jobs_bytes + tasks_bytes);
 
-  for (const Group& gr : groups) {
+  if (ntasks > 0) {
+    if (ctx->batch_grid == 0) {
+      int per_sm = 0, sms = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms::k_batch_tiles, kTileThreads,
+                                                        0) != cudaSuccess ||
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
+              cudaSuccess)
+        return MS_ERR_CUDA;
+      ctx->batch_grid = std::max(1, per_sm) * sms;
+    }
+    const int wpb = kTileThreads / 32;
+    const int grid = std::max(1, std::min(ctx->batch_grid, (ntasks + wpb - 1) / wpb));
+    if (cudaMemsetAsync(d_queue, 0, sizeof(int), s) != cudaSuccess) return MS_ERR_CUDA;
     ProfScope ps(ctx, s, kProfTile);
-    cudaError_t e = gr.fmt == MS_U8
-                        ? launch_group<MS_U8>(ctx->d_jobs + gr.first, gr.count, gr.ntiles, gr.P, s)
-                        : launch_group<MS_BITS32>(ctx->d_jobs + gr.first, gr.count, gr.ntiles,
-                                                  gr.P, s);
-    if (e != cudaSuccess) return MS_ERR_CUDA;
+    ms::k_batch_tiles<<<grid, kTileThreads, 0, s>>>(d_jobs, d_tasks, ntasks, d_queue);
+    if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
   }
   {
     ProfScope ps(ctx, s, kProfFixup);
-    k_fixup_mixed<<<count, ms::kFixWarps * 32, 0, s>>>(ctx->d_jobs, count);
+    k_fixup_mixed<<<count, ms::kFixWarps * 32, 0, s>>>(d_jobs, count);
   }
   return cuda_status(cudaGetLastError());
+}
+
+ms_status ms_autotune(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_result* outs_dev,
+                      ms_stream_t stream, ms_tuning* chosen) {
+  if (!ctx || !ins_host || !outs_dev || count < 1) return MS_ERR_INVALID;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (capturing(s)) return MS_ERR_UNSUPPORTED;
+  for (int32_t i = 0; i < count; ++i) {
+    ms_status st = check_matrix(&ins_host[i]);
+    if (st != MS_OK) return st;
+  }
+  DeviceGuard g(ctx->device);
+  const bool batch = count > 1;
+  const bool packed_single = !batch && ins_host[0].fmt == MS_BITS32;
+  std::vector<ms_tuning> cands;
+  const int rows[] = {0, 32, 64, 128, 256, 512, 1024};
+  for (int pp = 0; pp <= (packed_single ? 1 : 0); ++pp)
+    for (int r : rows) {
+      if (pp == 1 && r != 0) continue;  // the bitplane search has no band height
+      ms_tuning t{};
+      t.band_rows = r;
+      t.packed_path = pp;
+      cands.push_back(t);
+    }
+  const ms_tuning saved = ctx->tuning;
+  const auto saved_cache = ctx->tuned;
+  ctx->tuned.clear();
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MS_ERR_CUDA;
+  float best_ms = 1e30f;
+  ms_tuning best = cands[0];
+  ms_status err = MS_OK;
+  for (const ms_tuning& t : cands) {
+    ctx->tuning = t;
+    auto run = [&]() -> ms_status {
+      return batch ? ms_batch(ctx, ins_host, count, outs_dev, stream)
+                   : ms_max_square(ctx, ins_host, outs_dev, stream);
+    };
+    err = run();  // warm-up (also sizes the workspace)
+    if (err != MS_OK) break;
+    const int reps = 5;
+    cudaEventRecord(e0, s);
+    for (int k = 0; k < reps && err == MS_OK; ++k) err = run();
+    cudaEventRecord(e1, s);
+    if (err != MS_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      if (err == MS_OK) err = MS_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->tuning = saved;
+  ctx->tuned = saved_cache;
+  if (err != MS_OK) return err;
+  ctx->tuned[tune_class(ins_host, count, batch)] = best;
+  if (chosen) *chosen = best;
+  return MS_OK;
 }
 
 ms_status ms_profile_start(ms_ctx* ctx, int32_t max_launches) {

@@ -368,21 +368,11 @@ __device__ __forceinline__ int find_job(const Job* jobs, int njobs, int64_t t) {
   return lo;
 }
 
+// One warp, two tiles: compute, then publish each tile's key and the box of
+// its cells above the halo to its matrix's state.  jb < 0: no high tile.
 template <int P, int FMT, bool DPMAP>
-__device__ __forceinline__ void tile_pass_warp(const Job* jobs, int njobs, int64_t ntiles,
-                                               int64_t w) {
-  const int64_t t_a = 2 * w, t_b = 2 * w + 1;
-  if (t_a >= ntiles) return;
-  const int ja = find_job(jobs, njobs, t_a);
-  const Job& A = jobs[ja];
-  const Tile ga = tile_of(A, t_a - A.tile0);
-  int jb = -1;
-  Tile gb = empty_tile();
-  if (t_b < ntiles) {
-    jb = find_job(jobs, njobs, t_b);
-    gb = tile_of(jobs[jb], t_b - jobs[jb].tile0);
-  }
-  const Job& B = jobs[jb < 0 ? ja : jb];
+__device__ __forceinline__ void tile_pair(const Job& A, const Tile& ga, const Job& B,
+                                          const Tile& gb, bool has_b) {
   StripIO io{nullptr, nullptr, nullptr, nullptr, nullptr};
   Best ba, bb;
   run_tiles<P, FMT, DPMAP, 0>(ga, gb, A.dp, A.ld_dp, A.dp_aligned, B.dp, B.ld_dp, B.dp_aligned,
@@ -404,8 +394,8 @@ __device__ __forceinline__ void tile_pass_warp(const Job* jobs, int njobs, int64
       atomicMin(&A.st->box[2], ac0);
       atomicMax(&A.st->box[3], ac1);
     }
-    if (jb >= 0 && kb) atomicMax(&B.st->key, kb);
-    if (jb >= 0 && br1 >= 0) {
+    if (has_b && kb) atomicMax(&B.st->key, kb);
+    if (has_b && br1 >= 0) {
       atomicMin(&B.st->box[0], br0);
       atomicMax(&B.st->box[1], br1);
       atomicMin(&B.st->box[2], bc0);
@@ -414,16 +404,72 @@ __device__ __forceinline__ void tile_pass_warp(const Job* jobs, int njobs, int64
   }
 }
 
-// Size-only tiles fit 128 registers (two 256-thread blocks per SM); the dp-map
-// variant keeps more values live and runs one block per SM.
+// Warp w of a single-matrix launch takes tiles 2w and 2w+1.
 template <int P, int FMT, bool DPMAP>
-__global__ void __launch_bounds__(256, DPMAP ? 1 : 2) k_tiles(const Job* __restrict__ jobs,
-                                                               int njobs,
-                                               int64_t ntiles) {
-  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  tile_pass_warp<P, FMT, DPMAP>(jobs, njobs, ntiles, w);
+__device__ __forceinline__ void tile_pass_warp(const Job* jobs, int njobs, int64_t ntiles,
+                                               int64_t w) {
+  const int64_t t_a = 2 * w, t_b = 2 * w + 1;
+  if (t_a >= ntiles) return;
+  const int ja = find_job(jobs, njobs, t_a);
+  const Job& A = jobs[ja];
+  const Tile ga = tile_of(A, t_a - A.tile0);
+  int jb = -1;
+  Tile gb = empty_tile();
+  if (t_b < ntiles) {
+    jb = find_job(jobs, njobs, t_b);
+    gb = tile_of(jobs[jb], t_b - jobs[jb].tile0);
+  }
+  tile_pair<P, FMT, DPMAP>(A, ga, jobs[jb < 0 ? ja : jb], gb, jb >= 0);
 }
 
+// ---- batch: one persistent launch over a queue of tile pairs --------------
+
+struct PairTask {
+  int32_t job_a, job_b;  // job_b < 0: the high half is idle
+  int32_t tile_a, tile_b;
+};
+
+template <int P, int FMT>
+__device__ __forceinline__ void batch_task(const Job* jobs, const PairTask& t) {
+  const Job& A = jobs[t.job_a];
+  const bool has_b = t.job_b >= 0;
+  const Job& B = jobs[has_b ? t.job_b : t.job_a];
+  const Tile ga = tile_of(A, t.tile_a);
+  const Tile gb = has_b ? tile_of(B, t.tile_b) : empty_tile();
+  tile_pair<P, FMT, false>(A, ga, B, gb, has_b);
+}
+
+// Warps take tasks (tile pairs of one format and lane width, longest first)
+// from an atomic queue until it runs dry.
+static __global__ void __launch_bounds__(256, 2) k_batch_tiles(const Job* __restrict__ jobs,
+                                                        const PairTask* __restrict__ tasks,
+                                                        int ntasks, int* queue) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(queue, 1);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= ntasks) break;
+    const PairTask task = tasks[t];
+    const Job& A = jobs[task.job_a];
+    const int key = A.fmt * 32 + A.P;
+    switch (key) {
+      case MS_U8 * 32 + 1: batch_task<1, MS_U8>(jobs, task); break;
+      case MS_U8 * 32 + 2: batch_task<2, MS_U8>(jobs, task); break;
+      case MS_U8 * 32 + 4: batch_task<4, MS_U8>(jobs, task); break;
+      case MS_U8 * 32 + 8: batch_task<8, MS_U8>(jobs, task); break;
+      case MS_U8 * 32 + 16: batch_task<16, MS_U8>(jobs, task); break;
+      case MS_BITS32 * 32 + 1: batch_task<1, MS_BITS32>(jobs, task); break;
+      case MS_BITS32 * 32 + 2: batch_task<2, MS_BITS32>(jobs, task); break;
+      case MS_BITS32 * 32 + 4: batch_task<4, MS_BITS32>(jobs, task); break;
+      case MS_BITS32 * 32 + 8: batch_task<8, MS_BITS32>(jobs, task); break;
+      default: batch_task<16, MS_BITS32>(jobs, task); break;
+    }
+  }
+}
+
+// Size-only tiles fit 128 registers (two 256-thread blocks per SM); the dp-map
+// variant keeps more values live and runs one block per SM.
 // Single matrix: the job travels as a kernel parameter.
 template <int P, int FMT, bool DPMAP>
 __global__ void __launch_bounds__(256, DPMAP ? 1 : 2) k_tiles_one(const Job job, int64_t ntiles) {
@@ -433,7 +479,7 @@ __global__ void __launch_bounds__(256, DPMAP ? 1 : 2) k_tiles_one(const Job job,
 
 // ---- fix-up and result ------------------------------------------------------
 
-constexpr int kFixWarps = 16;
+constexpr int kFixWarps = 8;
 constexpr int kFixP = 8;            // short per-row chains: the fix-up is latency-bound
 constexpr int kFixW = 32 * kFixP;  // strip width in the fix-up
 

@@ -292,3 +292,28 @@ def test_packed_search_planted_and_closed_forms(packed_ctx):
         packed_ctx.set_tuning(packed_path=0)
         assert packed_ctx.max_square(x, n=n).cpu().tolist() == [K, r, c, 0], (m, n)
         packed_ctx.set_tuning(packed_path=1)
+
+
+def test_autotune_then_results_unchanged(ctx):
+    """The autotuner only changes launch parameters: results stay exact."""
+    rng = np.random.default_rng(31)
+    mats, exps = [], []
+    for i in range(40):
+        m, n = int(rng.integers(16, 700)), int(rng.integers(16, 900))
+        a = gen.bernoulli_u8(m, n, 0.85, seed=700 + i)
+        if i % 4 == 0:
+            s = int(rng.integers(1, min(m, n) + 1))
+            a[:s, n - s:] = 1
+        exps.append(list(oracle.dp(a, want_map=False)[0]) + [0])
+        mats.append(to_dev(a) if i % 2 else (bits_dev(a, n), n))
+    chosen = ctx.autotune(mats)
+    assert chosen["band_rows"] in (0, 32, 64, 128, 256, 512, 1024)
+    assert ctx.batch(mats).cpu().tolist() == exps
+    one = gen.bernoulli_u8(600, 3000, 0.9, seed=77)
+    one[100:400, 1000:1300] = 1
+    exp1 = list(oracle.dp(one, want_map=False)[0]) + [0]
+    w = bits_dev(one, 3000, ldw=96)
+    chosen1 = ctx.autotune([(w, 3000)])
+    assert chosen1["packed_path"] in (0, 1)
+    assert ctx.max_square(w, n=3000).cpu().tolist() == exp1
+    assert ctx.get_tuning()["band_rows"] == 0  # explicit tuning untouched
