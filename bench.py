@@ -18,6 +18,7 @@ Workloads (sizes from the configurations this benchmark mirrors):
   c3-u8 / c3-u8-dp / c3-bits / c3-bits-dp
            32768 x 32768, p = 0.9, one planted 600-square, seed 3
   c3q-*    the same with 8192 rows (for profiler captures)
+  c5       serving stream (see run_serve)
   c4       4096 uint8 matrices, m and n log-uniform in [16, 2048]: one autotuned
            ms_batch per step replayed from a CUDA graph (plain calls reported beside)
 """
@@ -621,6 +622,118 @@ def run_ours(args, world, rank, local, pg):
     ctx.close()
 
 
+def run_serve(args, world, rank, local, pg):
+    """Serving stream: Poisson arrivals of `--requests` requests, square sides
+    log-uniform in [64, 8192], density uniform in [0.1, 0.9], bit-packed input
+    from pinned host memory, 16 GB device admission budget.  Payloads are
+    quantised to 24 side classes x 9 densities (kept pinned in host memory)."""
+    import numpy as np
+    import torch
+
+    import gen
+    import paper_2503_18974_gb300 as ms
+    device = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(device)
+    ms.build()
+    rng = np.random.default_rng(5)
+    sides = np.unique(np.round(np.exp(np.linspace(np.log(64), np.log(8192), 24))).astype(int))
+    dens = np.arange(1, 10) / 10
+    nreq = args.requests
+    req_side = np.exp(rng.uniform(np.log(64), np.log(8192), nreq))
+    req_cls = np.abs(np.log(sides)[None, :] - np.log(req_side)[:, None]).argmin(1)
+    req_den = np.abs(dens[None, :] - rng.uniform(0.1, 0.9, nreq)[:, None]).argmin(1)
+    payload = {}
+    for c, d in set(zip(req_cls.tolist(), req_den.tolist())):
+        side = int(sides[c])
+        ldw = ((side + 31) // 32 + 3) // 4 * 4
+        dev = torch.empty((side, ldw), dtype=torch.int32, device=device)
+        gen.fill_bits_dev(dev.data_ptr(), side, side, ldw, float(dens[d]), 5000 + 16 * c + d)
+        host = torch.empty((side, ldw), dtype=torch.int32, pin_memory=True)
+        host.copy_(dev)
+        payload[(c, d)] = (host, dev, side)
+    torch.cuda.synchronize()
+    cells = sum(int(sides[c]) ** 2 for c in req_cls)
+
+    # results alone (the reference for "same alone and in the mix")
+    ctx = ms.MaxSquare(local)
+    alone = {}
+    for key, (host, dev, side) in payload.items():
+        alone[key] = ctx.max_square(dev, n=side).cpu().tolist()
+
+    def serve(rate):
+        srv = ms.Server(local, memory_budget=16 << 30, streams=3, max_batch=512)
+        srv.submit(payload[(req_cls[0], req_den[0])][0].numpy()[:1], n=64)  # warm
+        srv.wait_all()
+        srv.poll()
+        t0 = ms.now() + 0.01
+        arrivals = t0 + (np.cumsum(rng.exponential(1.0 / rate, nreq)) if rate else np.zeros(nreq))
+        ids = {}
+        for k in range(nreq):
+            while rate and ms.now() < arrivals[k]:
+                pass
+            key = (int(req_cls[k]), int(req_den[k]))
+            host, _, side = payload[key]
+            ids[srv.submit(host.numpy(), n=side, t_arrival=float(arrivals[k]))] = key
+        srv.wait_all()
+        done = srv.poll(nreq + 10)
+        st = srv.stats()
+        srv.close()
+        lat = np.array([c["t_done"] - c["t_submit"] for c in done])
+        span = max(c["t_done"] for c in done) - float(arrivals[0])
+        wrong = sum(1 for c in done if c["result"] != alone[ids[c["id"]]])
+        return {"cells_per_s": cells / span, "req_per_s": nreq / span, "span_s": span,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "wrong": wrong,
+                "batches": st["batches"], "peak_bytes": st["peak_bytes"],
+                "peak_inflight": st["peak_inflight"], "completed": len(done)}
+
+    sat = serve(0)
+    runs = {f"{f}x": serve(f * sat["req_per_s"]) for f in (0.5, 0.7, 0.9)}
+
+    # per-request plain launches, FIFO: copy in, ms_max_square, read back
+    buf = torch.empty(max(h.numel() for h, _, _ in payload.values()), dtype=torch.int32,
+                      device=device)
+    res = torch.empty(4, dtype=torch.int32, device=device)
+    res_h = torch.empty(4, dtype=torch.int32, pin_memory=True)
+    sub = min(nreq, 4000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain_cells = 0
+    for k in range(sub):
+        host, _, side = payload[(int(req_cls[k]), int(req_den[k]))]
+        d = buf[:host.numel()].view(host.shape)
+        d.copy_(host, non_blocking=True)
+        ctx.max_square(d, n=side, out=res)
+        res_h.copy_(res, non_blocking=True)
+        torch.cuda.synchronize()
+        plain_cells += side * side
+    plain = plain_cells / (time.perf_counter() - t0)
+    ctx.close()
+    r7 = runs["0.7x"]
+    if rank == 0:
+        line = {"metric": METRIC, "value": r7["cells_per_s"] / 1e9, "unit": "Gcells/s",
+                "n_gpus": world, "steps": 1, "warmup": 1,
+                "ms_per_step": r7["span_s"] * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bits32",
+                "data": "synthetic (seeded SplitMix64 Bernoulli matrices)",
+                "config": {"workload": f"serving stream: {nreq} Poisson requests at 0.7x the "
+                                       "saturated rate, sides log-uniform 64..8192, p in "
+                                       "0.1..0.9, bit-packed, 16 GB admission budget",
+                           "payload_classes": len(payload), "cells": cells},
+                "serve": {"saturated": sat, **runs},
+                "p50_ms": r7["p50_ms"], "p99_ms": r7["p99_ms"],
+                "plain_per_request": {"value": plain / 1e9, "unit": "Gcells/s",
+                                      "requests": sub,
+                                      "how": "FIFO, one H2D + ms_max_square + D2H per request"},
+                "e2e": {"value": r7["cells_per_s"] / 1e9, "unit": "Gcells/s",
+                        "h2d_bytes_per_step": int(cells // 8),
+                        "d2h_bytes_per_step": 16 * nreq,
+                        "how": "requests submitted from pinned host memory; latency includes "
+                               "queueing, copies and read-back"},
+                "roofline": None, "cpu_baseline": None, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -629,6 +742,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--packed-path", type=int, default=None,
                     help="1: bitplane search for packed size-only work (default for c3-bits)")
     args = ap.parse_args()
@@ -636,6 +750,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, world, rank, local, pg)
+        elif args.workload == "c5":
+            run_serve(args, world, rank, local, pg)
         else:
             run_ours(args, world, rank, local, pg)
     finally:

@@ -132,6 +132,56 @@ ms_status ms_max_square_noalloc(const ms_matrix* in, ms_result* out_dev, ms_stre
 /* Static, human-readable name of a status code. */
 const char* ms_status_string(ms_status st);
 
+/* ---- serving ----------------------------------------------------------------
+ * A request loop for a stream of independent detection requests (a library
+ * feature; the paper has no counterpart).  ms_server_submit hands the server
+ * a matrix in HOST memory (keep it valid until the request completes; pinned
+ * memory copies fastest) and returns at once.  A scheduler thread owned by
+ * the server then:
+ *   - admits requests in arrival order while their device input buffer fits
+ *     the memory budget (a request that could never fit is refused with
+ *     MS_ERR_BUDGET at submit); admitted buffers stay resident in a device
+ *     arena until the request completes;
+ *   - copies admitted inputs host->device on a copy stream;
+ *   - whenever one of `streams` compute streams is free, launches every
+ *     copied, not yet launched request (up to max_batch) as one ms_batch, so
+ *     requests arriving while others run join the next batch and batches on
+ *     different streams overlap (continuous batching);
+ *   - on completion reads the results back, frees the buffers and stamps the
+ *     request's times.
+ * Results are identical to ms_max_square on the same matrix.  Host clock
+ * times are seconds on a monotonic clock (ms_server_now). */
+typedef struct ms_server ms_server;
+
+typedef struct {
+  size_t memory_budget_bytes; /* device memory for resident request inputs */
+  int32_t streams;            /* concurrent batches (default 2) */
+  int32_t max_batch;          /* requests per batch (default 512) */
+  int32_t reserved[4];
+} ms_server_config;
+
+typedef struct {
+  uint64_t id;
+  ms_result result;
+  double t_submit, t_admit, t_launch, t_done;
+} ms_server_completion;
+
+typedef struct {
+  int64_t submitted, completed, batches;
+  int64_t peak_bytes;      /* largest arena use seen (never above the budget) */
+  int32_t peak_inflight;   /* largest number of batches on the device at once */
+  int32_t reserved;
+} ms_server_stats;
+
+ms_status ms_server_create(ms_server** out, int device, const ms_server_config* cfg);
+ms_status ms_server_submit(ms_server* srv, const ms_matrix* host_matrix, double t_arrival,
+                           uint64_t* id);  /* t_arrival < 0: now */
+ms_status ms_server_poll(ms_server* srv, ms_server_completion* out, int32_t max, int32_t* n_out);
+ms_status ms_server_wait_all(ms_server* srv);
+ms_status ms_server_stats_get(ms_server* srv, ms_server_stats* out);
+ms_status ms_server_destroy(ms_server* srv);
+double ms_server_now(void);
+
 /* ---- tuning -------------------------------------------------------------
  * Launch parameters: `band_rows` = rows of a matrix that one tile counts
  * (each tile also re-reads a halo of 32 rows above and 32 columns to its

@@ -19,9 +19,10 @@ from typing import Iterable, Sequence
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libms.so")
-_SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu", "ms_kernels.cuh",
-                                                      "ms_device.cuh", "ms_bits.cuh")]
-_UNITS = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu")]
+_SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu", "ms_serve.cu",
+                                                      "ms_kernels.cuh", "ms_device.cuh",
+                                                      "ms_bits.cuh")]
+_UNITS = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu", "ms_serve.cu")]
 _HEADER = os.path.join(_ROOT, "include", "ms.h")
 
 MS_U8 = 0
@@ -69,11 +70,35 @@ class Profile(ctypes.Structure):
                 ("untimed_launches", ctypes.c_int64)]
 
 
+class _Result(ctypes.Structure):
+    _fields_ = [("side", ctypes.c_int32), ("row", ctypes.c_int32), ("col", ctypes.c_int32),
+                ("status", ctypes.c_int32)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_size_t), ("streams", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("result", _Result), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
+                ("peak_inflight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 
 EXPORTS = ("ms_create", "ms_destroy", "ms_max_square", "ms_dp_map", "ms_batch",
            "ms_status_string", "ms_set_tuning", "ms_get_tuning", "ms_profile_start",
-           "ms_profile_stop", "ms_autotune", "ms_max_square_noalloc")
+           "ms_profile_stop", "ms_autotune", "ms_max_square_noalloc", "ms_server_create",
+           "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats_get",
+           "ms_server_destroy", "ms_server_now")
 
 
 def lib():
@@ -100,6 +125,23 @@ def lib():
         L.ms_set_tuning.argtypes = [vp, ctypes.POINTER(_Tuning)]
         L.ms_get_tuning.restype = ctypes.c_int
         L.ms_get_tuning.argtypes = [vp, ctypes.POINTER(_Tuning)]
+        L.ms_server_create.restype = ctypes.c_int
+        L.ms_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int,
+                                       ctypes.POINTER(ServerConfig)]
+        L.ms_server_submit.restype = ctypes.c_int
+        L.ms_server_submit.argtypes = [vp, ctypes.POINTER(_Matrix), ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_uint64)]
+        L.ms_server_poll.restype = ctypes.c_int
+        L.ms_server_poll.argtypes = [vp, ctypes.POINTER(Completion), ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_int32)]
+        L.ms_server_wait_all.restype = ctypes.c_int
+        L.ms_server_wait_all.argtypes = [vp]
+        L.ms_server_stats_get.restype = ctypes.c_int
+        L.ms_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.ms_server_destroy.restype = ctypes.c_int
+        L.ms_server_destroy.argtypes = [vp]
+        L.ms_server_now.restype = ctypes.c_double
+        L.ms_server_now.argtypes = []
         L.ms_autotune.restype = ctypes.c_int
         L.ms_autotune.argtypes = [vp, ctypes.POINTER(_Matrix), ctypes.c_int32, vp, vp,
                                   ctypes.POINTER(_Tuning)]
@@ -245,3 +287,81 @@ class MaxSquare:
 
 def status_string(code: int) -> str:
     return lib().ms_status_string(code).decode()
+
+
+def host_describe(a, n: int | None = None, fmt: int | None = None) -> _Matrix:
+    """ms_matrix for a 2-D host (numpy or CPU torch) array: uint8 cells or packed words."""
+    import numpy as np
+    arr = a.numpy() if hasattr(a, "numpy") else a
+    if arr.ndim != 2 or arr.strides[1] != arr.itemsize:
+        raise ValueError("expected a 2-D array with unit column stride")
+    if fmt is None:
+        fmt = MS_U8 if arr.dtype == np.uint8 else MS_BITS32
+    if fmt == MS_U8:
+        n = arr.shape[1] if n is None else n
+    elif n is None:
+        raise ValueError("MS_BITS32 needs the column count n")
+    ld = arr.strides[0] // arr.itemsize if arr.shape[0] > 1 else max(arr.shape[1], 1)
+    return _Matrix(arr.ctypes.data, arr.shape[0], n, ld, fmt, 0)
+
+
+class Server:
+    """The libms request server (admission by memory budget, continuous batching)."""
+
+    def __init__(self, device: int = 0, memory_budget: int = 16 << 30, streams: int = 2,
+                 max_batch: int = 512):
+        cfg = ServerConfig(memory_budget, streams, max_batch)
+        h = ctypes.c_void_p()
+        _check(lib().ms_server_create(ctypes.byref(h), device, ctypes.byref(cfg)),
+               "ms_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, a, n: int | None = None, fmt: int | None = None, t_arrival: float = -1.0,
+               keep=None) -> int:
+        """Submit a host matrix; it must stay alive until its completion is polled
+        (pass keep= to have the server object hold a reference)."""
+        desc = host_describe(a, n, fmt)
+        rid = ctypes.c_uint64()
+        _check(lib().ms_server_submit(self._h, ctypes.byref(desc), t_arrival, ctypes.byref(rid)),
+               "ms_server_submit")
+        self._keep[rid.value] = a if keep is None else keep
+        return rid.value
+
+    def poll(self, max_n: int = 4096) -> list:
+        buf = (Completion * max_n)()
+        n = ctypes.c_int32()
+        _check(lib().ms_server_poll(self._h, buf, max_n, ctypes.byref(n)), "ms_server_poll")
+        out = []
+        for k in range(n.value):
+            c = buf[k]
+            self._keep.pop(c.id, None)
+            out.append({"id": c.id, "result": [c.result.side, c.result.row, c.result.col,
+                                               c.result.status],
+                        "t_submit": c.t_submit, "t_admit": c.t_admit, "t_launch": c.t_launch,
+                        "t_done": c.t_done})
+        return out
+
+    def wait_all(self) -> None:
+        _check(lib().ms_server_wait_all(self._h), "ms_server_wait_all")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().ms_server_stats_get(self._h, ctypes.byref(st)), "ms_server_stats_get")
+        return {k: getattr(st, k) for k in ("submitted", "completed", "batches", "peak_bytes",
+                                            "peak_inflight")}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().ms_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def now() -> float:
+    return lib().ms_server_now()
