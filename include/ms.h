@@ -191,7 +191,12 @@ double ms_server_now(void);
 typedef struct {
   int32_t band_rows;
   int32_t packed_path;
-  int32_t reserved[6];
+  /* Test hook for failure detection, 0 in normal use: when 1, the first strip
+   * of the exact fix-up never publishes its carries, so the next strip's
+   * bounded wait (about 1 s) runs out and the matrix's ms_result.status is
+   * MS_ERR_TIMEOUT; later calls with the hook off are unaffected. */
+  int32_t test_hold_carries;
+  int32_t reserved[5];
 } ms_tuning;
 
 ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t);

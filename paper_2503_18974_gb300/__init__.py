@@ -60,7 +60,7 @@ class _Matrix(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("band_rows", ctypes.c_int32), ("packed_path", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("test_hold_carries", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class Profile(ctypes.Structure):
@@ -205,8 +205,9 @@ class MaxSquare:
         except Exception:
             pass
 
-    def set_tuning(self, band_rows: int = 0, packed_path: int = 0) -> None:
-        t = _Tuning(band_rows, packed_path)
+    def set_tuning(self, band_rows: int = 0, packed_path: int = 0,
+                   test_hold_carries: int = 0) -> None:
+        t = _Tuning(band_rows, packed_path, test_hold_carries)
         _check(lib().ms_set_tuning(self._h, ctypes.byref(t)), "ms_set_tuning")
 
     def profile_start(self, max_launches: int = 1 << 20) -> None:

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -27,6 +28,8 @@ struct ms_ctx {
   int64_t carry_cap = 0;  // in uint32
   int32_t* d_progress = nullptr;
   int64_t progress_cap = 0;
+  uint32_t* d_bitfix = nullptr;  // bitplanes of the size-only fix-up
+  int64_t bitfix_cap = 0;        // uint32 words
 
   // batch job table: device copy, the host image it was uploaded from, and a
   // pinned staging buffer guarded by an event
@@ -113,6 +116,22 @@ struct DeviceGuard {
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
   }
 };
+
+// Dynamic shared memory of a tile kernel launch: one input ring per warp.
+size_t ring_bytes(int threads) { return (size_t)(threads / 32) * ms::kRingWarpBytes; }
+
+// Raise a kernel's dynamic shared memory limit once (the rings exceed 48 KB).
+cudaError_t allow_smem(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<const void*, size_t> done;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find(fn);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[fn] = bytes;
+  return e;
+}
 
 bool capturing(cudaStream_t s) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -211,10 +230,19 @@ Job plan_job(const ms_tuning& tune, const ms_matrix* in) {
   j.aligned = (in->fmt == MS_U8) && (reinterpret_cast<uintptr_t>(in->data) % 16 == 0) &&
               (in->ld % 16 == 0);
   j.strips_fix = (int32_t)fix_strips_for(in->n);
+  j.test_hold = tune.test_hold_carries ? 1 : 0;
   return j;
 }
 
 int64_t tiles_of(const Job& j) { return (int64_t)j.bands * j.strips; }
+
+// Words of bitplane scratch the size-only fix-up of a matrix may need (three
+// planes over at most the whole matrix), and the pool cap beyond which
+// matrices fall back to the strip fix-up.
+int64_t bitfix_words(const Job& j) { return j.m > 0 && j.n > 0 ? 3 * j.m * ((j.n + 31) / 32 + 2) : 0; }
+constexpr int64_t kBitfixCapWords = (int64_t)1 << 30;  // 4 GiB
+
+
 
 ms_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MS_OK : MS_ERR_CUDA; }
 
@@ -289,17 +317,29 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
     const int64_t warps = (ntiles + 1) / 2;
     const int wpb = kTileThreads / 32;
     const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
+    const size_t sm = ring_bytes(kTileThreads);
     switch (j.P) {
-      case 1: ms::k_tiles_one<1, FMT, DPMAP><<<grid, kTileThreads, 0, s>>>(j, ntiles); break;
-      case 2: ms::k_tiles_one<2, FMT, DPMAP><<<grid, kTileThreads, 0, s>>>(j, ntiles); break;
-      case 4: ms::k_tiles_one<4, FMT, DPMAP><<<grid, kTileThreads, 0, s>>>(j, ntiles); break;
-      case 8: ms::k_tiles_one<8, FMT, DPMAP><<<grid, kTileThreads, 0, s>>>(j, ntiles); break;
-      default: ms::k_tiles_one<16, FMT, DPMAP><<<grid, kTileThreads, 0, s>>>(j, ntiles); break;
+#define MS_LAUNCH_TILES(PP)                                                             \
+  case PP:                                                                              \
+    if (allow_smem((const void*)ms::k_tiles_one<PP, FMT, DPMAP>, sm) != cudaSuccess)    \
+      return cudaGetLastError();                                                        \
+    ms::k_tiles_one<PP, FMT, DPMAP><<<grid, kTileThreads, sm, s>>>(j, ntiles);          \
+    break;
+      MS_LAUNCH_TILES(1)
+      MS_LAUNCH_TILES(2)
+      MS_LAUNCH_TILES(4)
+      MS_LAUNCH_TILES(8)
+      default:
+      MS_LAUNCH_TILES(16)
+#undef MS_LAUNCH_TILES
     }
   }
   {
     ProfScope ps(ctx, s, kProfFixup);
-    ms::k_fixup_one<FMT, DPMAP><<<1, ms::kFixWarps * 32, 0, s>>>(j);
+    const size_t sm = ring_bytes(ms::kFixWarps * 32);
+    if (allow_smem((const void*)ms::k_fixup_one<FMT, DPMAP>, sm) != cudaSuccess)
+      return cudaGetLastError();
+    ms::k_fixup_one<FMT, DPMAP><<<1, ms::kFixWarps * 32, sm, s>>>(j);
   }
   return cudaGetLastError();
 }
@@ -433,6 +473,10 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   Job j = plan_job(tune, in);
   st = ensure_workspace(ctx, 1, j.m * (int64_t)j.strips_fix, j.strips_fix, s);
   if (st != MS_OK) return st;
+  const int64_t bw = dp ? 0 : bitfix_words(j);
+  if (bw > 0 && bw <= kBitfixCapWords &&
+      grow(ctx, ctx->d_bitfix, ctx->bitfix_cap, bw, capturing(s)) == MS_OK)
+    j.bits_scratch = ctx->d_bitfix;
   j.tile0 = 0;
   j.dp = dp;
   j.ld_dp = ld_dp;
@@ -450,7 +494,7 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   return cuda_status(e);
 }
 
-__global__ void k_fixup_mixed(const Job* __restrict__ jobs, int njobs) {
+__global__ void __launch_bounds__(ms::kFixWarps * 32, 1) k_fixup_mixed(const Job* __restrict__ jobs, int njobs) {
   const int j = blockIdx.x;
   if (j >= njobs) return;
   const Job job = jobs[j];
@@ -520,6 +564,7 @@ ms_status ms_destroy(ms_ctx* ctx) {
     release(ctx, ctx->d_states, ctx->states_cap);
     release(ctx, ctx->d_carry, ctx->carry_cap);
     release(ctx, ctx->d_progress, ctx->progress_cap);
+    release(ctx, ctx->d_bitfix, ctx->bitfix_cap);
     release(ctx, ctx->d_table, ctx->table_cap);
     release(ctx, ctx->d_lvl, ctx->lvl_cap);
     release(ctx, ctx->d_act, ctx->act_cap);
@@ -539,6 +584,7 @@ ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t) {
   if (!ctx || !t) return MS_ERR_INVALID;
   if (t->band_rows < 0 || t->band_rows > 65000) return MS_ERR_INVALID;
   if (t->packed_path < 0 || t->packed_path > 1) return MS_ERR_INVALID;
+  if (t->test_hold_carries < 0 || t->test_hold_carries > 1) return MS_ERR_INVALID;
   ctx->tuning = *t;
   return MS_OK;
 }
@@ -598,7 +644,12 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   // length, longest first, form the queue of the persistent launch
   struct TileRef { int32_t job, tile, steps; };
   std::vector<std::vector<TileRef>> groups(2 * 32);
-  int64_t carry_off = 0, prog_off = 0;
+  int64_t carry_off = 0, prog_off = 0, bit_need = 0;
+  for (int32_t i = 0; i < count; ++i) bit_need += bitfix_words(jobs[i]);
+  bit_need = std::min(bit_need, kBitfixCapWords);
+  if (bit_need > 0 && grow(ctx, ctx->d_bitfix, ctx->bitfix_cap, bit_need, cap) != MS_OK)
+    bit_need = 0;
+  int64_t bit_off = 0;
   for (int32_t i = 0; i < count; ++i) {
     Job& j = jobs[i];
     j.tile0 = 0;
@@ -608,6 +659,12 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     j.progress = ctx->d_progress + prog_off;
     carry_off += j.m * (int64_t)j.strips_fix;
     prog_off += j.strips_fix;
+    const int64_t bw = bitfix_words(j);
+    j.bits_scratch = nullptr;
+    if (bw > 0 && bit_off + bw <= bit_need) {
+      j.bits_scratch = ctx->d_bitfix + bit_off;
+      bit_off += bw;
+    }
     const int64_t nt = tiles_of(j);
     auto& g = groups[j.fmt * 32 + j.P];
     for (int64_t t = 0; t < nt; ++t) g.push_back(TileRef{i, (int32_t)t, tile_steps(j, t)});
@@ -675,10 +732,12 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   int* d_queue = reinterpret_cast<int*>(ctx->d_table + jobs_bytes + tasks_bytes);
 
   if (ntasks > 0) {
+    const size_t sm = ring_bytes(kTileThreads);
+    if (allow_smem((const void*)ms::k_batch_tiles, sm) != cudaSuccess) return MS_ERR_CUDA;
     if (ctx->batch_grid == 0) {
       int per_sm = 0, sms = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms::k_batch_tiles, kTileThreads,
-                                                        0) != cudaSuccess ||
+                                                        sm) != cudaSuccess ||
           cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
               cudaSuccess)
         return MS_ERR_CUDA;
@@ -688,12 +747,14 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     const int grid = std::max(1, std::min(ctx->batch_grid, (ntasks + wpb - 1) / wpb));
     if (cudaMemsetAsync(d_queue, 0, sizeof(int), s) != cudaSuccess) return MS_ERR_CUDA;
     ProfScope ps(ctx, s, kProfTile);
-    ms::k_batch_tiles<<<grid, kTileThreads, 0, s>>>(d_jobs, d_tasks, ntasks, d_queue);
+    ms::k_batch_tiles<<<grid, kTileThreads, sm, s>>>(d_jobs, d_tasks, ntasks, d_queue);
     if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
   }
   {
     ProfScope ps(ctx, s, kProfFixup);
-    k_fixup_mixed<<<count, ms::kFixWarps * 32, 0, s>>>(d_jobs, count);
+    const size_t smf = ring_bytes(ms::kFixWarps * 32);
+    if (allow_smem((const void*)k_fixup_mixed, smf) != cudaSuccess) return MS_ERR_CUDA;
+    k_fixup_mixed<<<count, ms::kFixWarps * 32, smf, s>>>(d_jobs, count);
   }
   return cuda_status(cudaGetLastError());
 }

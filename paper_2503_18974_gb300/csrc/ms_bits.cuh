@@ -108,8 +108,9 @@ __device__ __forceinline__ void grid_barrier(State* st) {
       st_release(reinterpret_cast<int32_t*>(&st->bar_gen), (int)(gen + 1));
     } else {
       int spins = 0;
+      const unsigned long long t0 = global_ns();
       while ((unsigned)ld_acquire(reinterpret_cast<const int32_t*>(&st->bar_gen)) == gen) {
-        if (++spins > kSpinLimit) {
+        if (++spins > kSpinLimit || global_ns() - t0 > kWaitLimitNs) {
           atomicExch(&st->err, (int)MS_ERR_TIMEOUT);
           break;
         }

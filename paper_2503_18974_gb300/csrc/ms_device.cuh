@@ -26,7 +26,8 @@ constexpr uint32_t kBias = 64;             // row offset so that every value sta
 constexpr int kHalo = 32;                  // halo rows above / columns left of a tile
 constexpr uint64_t kKeyMask = (1ull << 40) - 1;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kSpinLimit = 1 << 22;        // bounded waits (x ~100 ns sleep => ~0.4 s)
+constexpr int kSpinLimit = 1 << 22;        // iteration cap of bounded waits
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a wait gives up after ~1 s
 
 // ---- per-matrix job description and state ---------------------------------
 
@@ -55,7 +56,8 @@ struct Job {
   uint32_t* carry;         // fix-up strip carries: strips_fix rows each
   int32_t* progress;       // fix-up per-strip published row counts
   int32_t strips_fix;      // capacity of carry/progress in strips
-  int32_t pad2;
+  int32_t test_hold;       // test hook: the first fix-up strip never publishes carries
+  uint32_t* bits_scratch;  // size-only fix-up bitplanes (3 x m x (ceil(n/32)+2) words), or null
 };
 
 // ---- 16x2 SIMD helpers ---------------------------------------------------
@@ -89,6 +91,12 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
 // Marks each nonzero byte of x with its most significant bit (other bits are junk).
 __device__ __forceinline__ uint32_t nonzero_msb(uint32_t x) {
   return ((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
 __device__ __forceinline__ int ld_acquire(const int32_t* p) {

@@ -83,63 +83,116 @@ __device__ __forceinline__ Tile empty_tile() {
   return g;
 }
 
-// Streams one lane's column chunk of a tile down the window, one row per
-// call, with the address and the bounds decisions fixed once per tile.
-template <int P, int FMT>
-struct LaneReader {
-  const uint8_t* ptr;  // chunk of window row `row`
-  int64_t stride;      // bytes between rows
-  int row, nrows;
-  int mode;            // 0: no cells, 1: full aligned chunk, 2: edge or unaligned chunk
-  int nvalid;          // mode 2: cells of the chunk left of column n
+// ---- input staging ---------------------------------------------------------
+// Each warp owns a ring of kRing slots in shared memory; a slot holds one row
+// step of both tiles: [tile][lane][16 bytes].  Lane l copies its own column
+// chunk of window row (s - l + kRing) into the slot it consumes at step s with
+// cp.async (no registers held while the copy is in flight), so loads run
+// kRing steps ahead of use.  Edge and unaligned chunks, and chunks of fewer
+// than 4 bytes, are loaded synchronously into the same slot.
+constexpr int kRing = 8;
+constexpr int kRingSlotBytes = 2 * 32 * 16;
+constexpr int kRingWarpBytes = kRing * kRingSlotBytes;
 
-  __device__ __forceinline__ void init(const Tile& g, int lane, int first_row) {
+__device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int bytes_copy,
+                                         int bytes_src) {
+  if (bytes_copy == 16)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(bytes_src) : "memory");
+  else if (bytes_copy == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src),
+                 "r"(bytes_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
+                 "r"(bytes_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Streams one lane's column chunk of a tile down the window into its ring.
+template <int P, int FMT>
+struct AsyncReader {
+  static constexpr int kBytes = FMT == MS_U8 ? P : 4;  // chunk bytes
+  const uint8_t* ptr;   // chunk of window row `row`
+  const uint8_t* safe;  // a valid address (zero-fill copies read nothing)
+  int64_t stride;
+  int row, nrows;
+  int mode;             // 0: no cells (slots stay zero), 1: async copy, 2: synchronous
+  int nvalid;
+  uint32_t dst;         // this lane's place in slot 0
+
+  __device__ __forceinline__ void init(const Tile& g, int lane, int first_row, uint32_t ring,
+                                       int half) {
     const int64_t col = g.wc0 + (int64_t)P * lane;
     row = first_row;
     nrows = g.nrows;
+    dst = ring + half * 512 + lane * 16;
+    safe = g.base;
     if constexpr (FMT == MS_U8) {
       stride = g.ld;
       ptr = g.base + (g.wr0 + first_row) * g.ld + col;
       const int64_t valid = g.n - col;
       nvalid = (int)(valid < P ? (valid < 0 ? 0 : valid) : P);
-      mode = nvalid == 0 ? 0 : ((nvalid == P && g.aligned) ? 1 : 2);
+      mode = nvalid == 0 ? 0 : ((nvalid == P && g.aligned && P >= 4) ? 1 : 2);
     } else {
       stride = g.ld * 4;
       ptr = g.base + ((g.wr0 + first_row) * g.ld + (col >> 5)) * 4;
-      nvalid = 0;
+      nvalid = 4;
       mode = col < g.n ? 1 : 0;
     }
+    // slots start as zeros: mode 0 never writes, the others overwrite
+#pragma unroll
+    for (int k = 0; k < kRing; ++k)
+      asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst + k * kRingSlotBytes),
+                   "r"(0u) : "memory");
   }
 
-  __device__ __forceinline__ void next(Raw<P, FMT>& r) {
+  // copy window row `row` into `slot` and advance
+  __device__ __forceinline__ void issue(int slot) {
     const bool ok = (unsigned)row < (unsigned)nrows;
-    if constexpr (FMT == MS_U8) {
-#pragma unroll
-      for (int i = 0; i < Raw<P, MS_U8>::W; ++i) r.w[i] = 0;
-      if (ok && mode == 1) {
-        if constexpr (P == 16) {
-          const uint4 v = __ldg(reinterpret_cast<const uint4*>(ptr));
-          r.w[0] = v.x; r.w[1] = v.y; r.w[2] = v.z; r.w[3] = v.w;
-        } else if constexpr (P == 8) {
-          const uint2 v = __ldg(reinterpret_cast<const uint2*>(ptr));
-          r.w[0] = v.x; r.w[1] = v.y;
-        } else if constexpr (P == 4) {
-          r.w[0] = __ldg(reinterpret_cast<const uint32_t*>(ptr));
-        } else if constexpr (P == 2) {
-          r.w[0] = __ldg(reinterpret_cast<const uint16_t*>(ptr));
-        } else {
-          r.w[0] = __ldg(ptr);
-        }
-      } else if (ok && mode == 2) {
-        for (int b = 0; b < nvalid; ++b) r.w[b >> 2] |= (uint32_t)__ldg(ptr + b) << (8 * (b & 3));
-      }
-    } else {
-      r.word = (ok && mode == 1) ? __ldg(reinterpret_cast<const uint32_t*>(ptr)) : 0u;
+    const uint32_t d = dst + slot * kRingSlotBytes;
+    if (mode == 1) {
+      cp_async(d, ok ? (const void*)ptr : (const void*)safe, kBytes, ok ? kBytes : 0);
+    } else if (mode == 2) {
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      if (ok)
+        for (int b = 0; b < nvalid; ++b) w[b >> 2] |= (uint32_t)__ldg(ptr + b) << (8 * (b & 3));
+      asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(d), "r"(w[0]), "r"(w[1]),
+                   "r"(w[2]), "r"(w[3]) : "memory");
     }
     ptr += stride;
     ++row;
   }
+
+  __device__ __forceinline__ void read(int slot, Raw<P, FMT>& r) const {
+    const uint32_t a = dst + slot * kRingSlotBytes;
+    if constexpr (FMT == MS_U8) {
+      if constexpr (Raw<P, MS_U8>::W == 4) {
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3])
+                     : "r"(a) : "memory");
+      } else if constexpr (Raw<P, MS_U8>::W == 2) {
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.w[0]), "=r"(r.w[1]) : "r"(a)
+                     : "memory");
+      } else {
+        asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r.w[0]) : "r"(a) : "memory");
+      }
+    } else {
+      asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r.word) : "r"(a) : "memory");
+    }
+  }
 };
+
+// This warp's ring in the block's dynamic shared memory (warps x kRingWarpBytes).
+__device__ __forceinline__ uint32_t warp_ring() {
+  extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
+  return (uint32_t)__cvta_generic_to_shared(ms_dyn_smem) + (threadIdx.x >> 5) * kRingWarpBytes;
+}
 
 // Left-edge carries of a strip in the fix-up (mode 1).
 struct StripIO {
@@ -148,6 +201,7 @@ struct StripIO {
   uint32_t* carry_out;        // null for the last strip
   int32_t* progress_out;
   int32_t* status;
+  int32_t hold;               // test hook: never publish (the neighbour's wait must time out)
 };
 
 // Writes one lane's dp values of one row (half `hi` of the packed A values).
@@ -180,11 +234,13 @@ __device__ __forceinline__ void store_dp(int32_t* p, const uint32_t* Ap, uint32_
 template <int P, int FMT, bool DPMAP, int MODE>
 __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_t* dpa,
                                           int64_t lda, int dpa_al, int32_t* dpb, int64_t ldb,
-                                          int dpb_al, const StripIO& io, Best& ba, Best& bb) {
+                                          int dpb_al, const StripIO& io, Best& ba, Best& bb,
+                                          uint32_t ring) {
   const int lane = threadIdx.x & 31;
   constexpr uint32_t kB2 = kBias * 0x10001u;
   constexpr uint32_t kClamp2 = (kBias - 1) * 0x10001u;
-  constexpr int D = 4;  // rows of input prefetched per lane
+  constexpr int D = kRing;  // rows of input in flight per lane
+  static_assert((D & (D - 1)) == 0, "the ring size must be a power of two");
   const int nmax = max(ta.nrows, tb.nrows);
   const int nsteps = nmax + 31;
 
@@ -217,27 +273,32 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
   int32_t* dprow_a = DPMAP && dpa ? dpa + ta.wr0 * lda + cola : nullptr;
   int32_t* dprow_b = DPMAP && dpb ? dpb + tb.wr0 * ldb + colb : nullptr;
 
-  LaneReader<P, FMT> rda, rdb;
-  rda.init(ta, lane, -lane);
-  rdb.init(tb, lane, -lane);
-  Raw<P, FMT> lo[D], hi[D];
+  AsyncReader<P, FMT> rda, rdb;
+  rda.init(ta, lane, -lane, ring, 0);
+  rdb.init(tb, lane, -lane, ring, 1);
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    rda.next(lo[d]);
-    rdb.next(hi[d]);
+    rda.issue(d);
+    rdb.issue(d);
+    cp_async_commit();
   }
 
-  for (int s0 = 0; s0 < nsteps; s0 += D) {
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const int s = s0 + d;
+  // one step per iteration, not unrolled: the ring slot is a shared-memory
+  // address computed at run time, and a rolled loop keeps the kernel small
+  // enough for the instruction cache
+#pragma unroll 1
+  for (int s = 0; s < nsteps; ++s) {
+    {
+      const int d = s & (D - 1);
       const int ir = s - lane;
       uint32_t qn = __shfl_up_sync(kFull, pubQ, 1);
       uint32_t an = __shfl_up_sync(kFull, pubA, 1);
-      const Cells<P, FMT> clo = cells_of<P>(lo[d], lca);
-      const Cells<P, FMT> chi = cells_of<P>(hi[d], lcb);
-      rda.next(lo[d]);
-      rdb.next(hi[d]);
+      cp_async_wait<D - 1>();
+      Raw<P, FMT> rlo, rhi;
+      rda.read(d, rlo);
+      rdb.read(d, rhi);
+      const Cells<P, FMT> clo = cells_of<P>(rlo, lca);
+      const Cells<P, FMT> chi = cells_of<P>(rhi, lcb);
       if ((unsigned)ir < (unsigned)nmax) {
         const uint32_t I = (uint32_t)ir + 1u + kBias;
         const uint32_t I2 = I * 0x10001u;
@@ -249,8 +310,9 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
             if (io.carry_in) {
               if (!gave_up) {
                 int spins = 0;
+                const unsigned long long t0 = global_ns();
                 while (ld_acquire(io.progress_in) <= ir) {
-                  if (++spins > kSpinLimit) {
+                  if (++spins > kSpinLimit || global_ns() - t0 > kWaitLimitNs) {
                     gave_up = true;
                     atomicExch(io.status, (int)MS_ERR_TIMEOUT);
                     break;
@@ -285,7 +347,7 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
         if constexpr (MODE == 1) {
           if (lane == 31 && io.carry_out) {
             io.carry_out[ir] = (Q & 0xffffu) | (Ap[P - 1] << 16);
-            if (((ir + 1) & 7) == 0 || ir + 1 == ta.nrows) {
+            if ((((ir + 1) & 7) == 0 || ir + 1 == ta.nrows) && !io.hold) {
               __threadfence();
               st_release(io.progress_out, ir + 1);
             }
@@ -348,8 +410,13 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
             store_dp<P, true>(dprow_b + (int64_t)ir * ldb, Ap, I, colb, tb.n, dpb_al);
         }
       }
+      // the slot just consumed receives the row D steps ahead
+      rda.issue(d);
+      rdb.issue(d);
+      cp_async_commit();
     }
   }
+  cp_async_wait<0>();
 }
 
 // Reduce a per-lane best to the tile's key; returns the tile's largest value.
@@ -373,10 +440,10 @@ __device__ __forceinline__ int find_job(const Job* jobs, int njobs, int64_t t) {
 template <int P, int FMT, bool DPMAP>
 __device__ __forceinline__ void tile_pair(const Job& A, const Tile& ga, const Job& B,
                                           const Tile& gb, bool has_b) {
-  StripIO io{nullptr, nullptr, nullptr, nullptr, nullptr};
+  StripIO io{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
   Best ba, bb;
   run_tiles<P, FMT, DPMAP, 0>(ga, gb, A.dp, A.ld_dp, A.dp_aligned, B.dp, B.ld_dp, B.dp_aligned,
-                              io, ba, bb);
+                              io, ba, bb, warp_ring());
   const unsigned long long ka = tile_key(ba, ga.n);
   const unsigned long long kb = tile_key(bb, gb.n);
   // the tile's cells above the halo: bounding box over the warp's lanes
@@ -479,9 +546,178 @@ __global__ void __launch_bounds__(256, DPMAP ? 1 : 2) k_tiles_one(const Job job,
 
 // ---- fix-up and result ------------------------------------------------------
 
-constexpr int kFixWarps = 8;
+constexpr int kFixWarps = 16;
 constexpr int kFixP = 8;            // short per-row chains: the fix-up is latency-bound
 constexpr int kFixW = 32 * kFixP;  // strip width in the fix-up
+
+// ---- size-only fix-up by bitplane growth inside the box ------------------
+//
+// S_t = bottom-right corners of all-ones t-squares.  Every cell with dp >= 33
+// has a window value above the halo and lies in the flagged box, so S_t for
+// t >= 33 lies inside the box.  S_32 is exact everywhere; it is built from the
+// input on the box grown by 32 up and left, then squares are grown inside the
+// box: S_{a+b-1} = S_a & S_a(i-b+1, j) & S_a(i, j-b+1) & S_a(i-b+1, j-b+1)
+// (doubling from 32, then binary search), and the witness is the first set
+// bit of S_K.  One CTA per matrix; passes are separated by __syncthreads.
+
+struct Plane {  // a bitplane over rows [r0, r1) and words [w0, w1), zero outside
+  uint32_t* p;
+  int64_t r0, r1, w0, w1;
+  __device__ __forceinline__ uint32_t get(int64_t i, int64_t w) const {
+    return (i >= r0 && i < r1 && w >= w0 && w < w1) ? p[(i - r0) * (w1 - w0) + (w - w0)] : 0u;
+  }
+};
+
+// 32 cells of input row i starting at column 32*w, as bits (columns >= n: 0).
+template <int FMT>
+__device__ __forceinline__ uint32_t input_word(const Job& j, int64_t i, int64_t w) {
+  const int64_t c = 32 * w;
+  if (i < 0 || i >= j.m || w < 0 || c >= j.n) return 0u;
+  const int64_t valid = j.n - c;
+  const uint32_t mask = valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u);
+  if constexpr (FMT == MS_BITS32) {
+    return __ldg(reinterpret_cast<const uint32_t*>(j.data) + i * j.ld + w) & mask;
+  } else {
+    const uint8_t* row = reinterpret_cast<const uint8_t*>(j.data) + i * j.ld + c;
+    uint32_t bits = 0;
+    const int lim = valid >= 32 ? 32 : (int)valid;
+    for (int b = 0; b < lim; ++b) bits |= (uint32_t)(__ldg(row + b) != 0) << b;
+    return bits;
+  }
+}
+
+// out = grow(L, d) on plane O (rows/words of O), returns whether any bit is set.
+__device__ __forceinline__ bool grow_pass(const Plane& L, const Plane& O, int64_t d, int64_t n,
+                                          bool write, unsigned long long* first) {
+  const int q = (int)(d >> 5), r = (int)(d & 31);
+  const int64_t W = O.w1 - O.w0, total = (O.r1 - O.r0) * W;
+  bool any = false;
+  unsigned long long f = ~0ull;
+#pragma unroll 4
+  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
+    const int64_t i = O.r0 + e / W, w = O.w0 + e % W;
+    const uint32_t a0 = L.get(i, w), a1 = L.get(i - d, w);
+    uint32_t a2 = L.get(i, w - q), a3 = L.get(i - d, w - q);
+    if (r) {
+      a2 = (a2 << r) | (L.get(i, w - q - 1) >> (32 - r));
+      a3 = (a3 << r) | (L.get(i - d, w - q - 1) >> (32 - r));
+    }
+    const int64_t valid = n - 32 * w;
+    const uint32_t cm = valid >= 32 ? 0xffffffffu : (valid <= 0 ? 0u : ((1u << valid) - 1u));
+    const uint32_t v = a0 & a1 & a2 & a3 & cm;
+    if (write) O.p[e] = v;
+    if (v) {
+      any = true;
+      if (first) {
+        const unsigned long long cand =
+            (unsigned long long)i * (unsigned long long)n + (unsigned long long)(32 * w) +
+            (unsigned long long)(__ffs(v) - 1);
+        f = cand < f ? cand : f;
+      }
+    }
+  }
+  if (first && f != ~0ull) atomicMin(first, f);
+  return __syncthreads_or(any ? 1 : 0) != 0;
+}
+
+template <int FMT>
+__device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int clo, int chi) {
+  __shared__ unsigned long long s_first;
+  const int64_t ra = max(0, rlo - kHalo);
+  const int64_t wlo = clo / 32, whi = (chi + 31) / 32;
+  const int64_t wa = max(0, clo - kHalo) / 32;
+  const int64_t R1 = rhi - ra, W1 = whi - wa;
+  const int64_t cap = j.m * ((j.n + 31) / 32 + 2);
+  uint32_t* buf0 = j.bits_scratch;            // V_32 (vertical runs >= 32), then levels
+  uint32_t* buf1 = j.bits_scratch + cap;      // S_32 on the grown box
+  uint32_t* buf2 = j.bits_scratch + 2 * cap;  // packed input, then levels
+  // 1. input bits of rows [pa, rhi), words [wa-1, whi)
+  const int64_t pa = max((int64_t)0, ra - 31);
+  const int64_t Wv = W1 + 1, RP = rhi - pa;
+#pragma unroll 4
+  for (int64_t e = threadIdx.x; e < RP * Wv; e += blockDim.x)
+    buf2[e] = input_word<FMT>(j, pa + e / Wv, wa - 1 + e % Wv);
+  __syncthreads();
+  // 2. vertical: V_32(i, w) = AND of the 32 rows ending at i, by doubling
+  //    V_2k(i) = V_k(i) & V_k(i-k) over rows [pa, rhi) (5 passes, ping-pong
+  //    between buf2 and buf0).  Rows above pa read as zeros, so V_k is exact
+  //    on rows >= pa + k - 1, which covers every row >= ra (pa = ra - 31, or
+  //    pa = 0 at the matrix top where the zeros are real).
+  {
+    uint32_t* src = buf2;
+    uint32_t* dst = buf0;
+    for (int k = 1; k < 32; k *= 2) {
+#pragma unroll 4
+      for (int64_t e = threadIdx.x; e < RP * Wv; e += blockDim.x) {
+        const int64_t i = pa + e / Wv;
+        const uint32_t up = (i - k >= pa) ? src[e - (int64_t)k * Wv] : 0u;
+        dst[e] = src[e] & up;
+      }
+      __syncthreads();
+      uint32_t* t = src;
+      src = dst;
+      dst = t;
+    }
+    if (src != buf0)
+      for (int64_t e = threadIdx.x; e < RP * Wv; e += blockDim.x) buf0[e] = src[e];
+    __syncthreads();
+  }
+  // 3. horizontal: S_32 = AND of 32 consecutive V_32 bits ending at each cell
+  for (int64_t e = threadIdx.x; e < R1 * W1; e += blockDim.x) {
+    const int64_t ii = e / W1, col = e % W1;
+    const int64_t vr = ii + (ra - pa);  // row of V_32 in its [pa, rhi) layout
+    const uint32_t x = buf0[vr * Wv + col + 1], y = buf0[vr * Wv + col];
+    unsigned long long z = ((unsigned long long)x << 32) | y;
+    z &= z << 1;
+    z &= z << 2;
+    z &= z << 4;
+    z &= z << 8;
+    z &= z << 16;
+    buf1[e] = (uint32_t)(z >> 32);
+  }
+  __syncthreads();
+  const Plane s32{buf1, ra, rhi, wa, whi};
+  // 3. doubling from 32 inside the box, then binary search
+  const Plane box0{buf0, rlo, rhi, wlo, whi}, box2{buf2, rlo, rhi, wlo, whi};
+  Plane cur = s32, nxt = box0;
+  int64_t a = 32, lo, hi;
+  const int64_t kmax = min(j.m, j.n);
+  for (;;) {
+    if (2 * a > kmax) {
+      lo = a;
+      hi = kmax + 1;
+      break;
+    }
+    const bool ne = grow_pass(cur, nxt, a, j.n, true, nullptr);
+    __syncthreads();
+    if (!ne) {
+      lo = a;
+      hi = 2 * a;
+      break;
+    }
+    a *= 2;
+    const Plane done = cur;
+    cur = nxt;
+    nxt = (done.p == buf1) ? box2 : done;
+  }
+  while (hi - lo > 1) {
+    const int64_t t = (lo + hi) / 2;
+    const bool ne = grow_pass(cur, box0, t - a, j.n, false, nullptr);
+    if (ne) lo = t; else hi = t;
+  }
+  // 4. witness: the first set bit of S_lo inside the box
+  if (threadIdx.x == 0) s_first = ~0ull;
+  __syncthreads();
+  const Plane wbox{nullptr, rlo, rhi, wlo, whi};
+  grow_pass(cur, wbox, lo - a, j.n, false, &s_first);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_first != ~0ull) {
+    const unsigned long long idx = s_first;
+    atomicMax(&j.st->key, make_key((int32_t)lo, (int64_t)(idx / (unsigned long long)j.n),
+                                   (int64_t)(idx % (unsigned long long)j.n), j.n));
+  }
+  __syncthreads();
+}
 
 template <int FMT, bool DPMAP>
 __device__ __forceinline__ void fixup_job(const Job& j) {
@@ -495,7 +731,9 @@ __device__ __forceinline__ void fixup_job(const Job& j) {
   }
   __syncthreads();
   const int rlo = sbox[0], rhi = sbox[1], clo = sbox[2], chi = sbox[3];
-  if (rhi > rlo && chi > clo) {
+  if (!DPMAP && j.bits_scratch && rhi > rlo && chi > clo) {
+    fixup_bits<FMT>(j, rlo, rhi, clo, chi);
+  } else if (rhi > rlo && chi > clo) {
     const int64_t br0 = max(0, rlo - kHalo);
     // rounded down to 32 columns: fix-up chunks must stay inside a packed
     // word and keep vector loads aligned (a wider window is still exact)
@@ -521,9 +759,10 @@ __device__ __forceinline__ void fixup_job(const Job& j) {
       io.carry_out = (s + 1 < nstrips) ? j.carry + (int64_t)s * j.m : nullptr;
       io.progress_out = j.progress + s;
       io.status = &st->status;
+      io.hold = (s == 0) ? j.test_hold : 0;
       Best ba, bb;
       run_tiles<kFixP, FMT, DPMAP, 1>(g, empty_tile(), j.dp, j.ld_dp, j.dp_aligned, nullptr, 0, 0,
-                                      io, ba, bb);
+                                      io, ba, bb, warp_ring());
       const unsigned long long ka = tile_key(ba, j.n);
       if ((threadIdx.x & 31) == 0 && ka) atomicMax(&st->key, ka);
     }
@@ -558,7 +797,7 @@ __device__ __forceinline__ void fixup_job(const Job& j) {
 }
 
 template <int FMT, bool DPMAP>
-__global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* __restrict__ jobs,
+__global__ void __launch_bounds__(kFixWarps * 32, 1) k_fixup(const Job* __restrict__ jobs,
                                                           int njobs) {
   const int j = blockIdx.x;
   if (j >= njobs) return;
@@ -568,7 +807,7 @@ __global__ void __launch_bounds__(kFixWarps * 32) k_fixup(const Job* __restrict_
 }
 
 template <int FMT, bool DPMAP>
-__global__ void __launch_bounds__(kFixWarps * 32) k_fixup_one(const Job job) {
+__global__ void __launch_bounds__(kFixWarps * 32, 1) k_fixup_one(const Job job) {
   fixup_job<FMT, DPMAP>(job);
 }
 

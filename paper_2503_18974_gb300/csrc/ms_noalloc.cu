@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_noalloc_tiles(const ms::Job job, i
 }
 
 template <int FMT>
-__global__ void __launch_bounds__(ms::kFixWarps * 32) k_noalloc_fixup(const ms::Job job) {
+__global__ void __launch_bounds__(ms::kFixWarps * 32, 1) k_noalloc_fixup(const ms::Job job) {
   ms::fixup_job<FMT, false>(job);
 }
 
@@ -110,20 +110,36 @@ int pairs_for(int64_t n) {
   return 16;
 }
 
+// Raise a kernel's dynamic shared memory limit (its per-warp input rings).
+cudaError_t allow_smem(const void* fn, int bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 template <int FMT>
 cudaError_t launch(const ms::Job& j, int64_t ntiles, cudaStream_t s) {
   if (ntiles > 0) {
     const int64_t warps = (ntiles + 1) / 2;
     const unsigned grid = (unsigned)((warps + kThreads / 32 - 1) / (kThreads / 32));
+    const int sm = (kThreads / 32) * ms::kRingWarpBytes;
     switch (j.P) {
-      case 1: k_noalloc_tiles<1, FMT><<<grid, kThreads, 0, s>>>(j, ntiles); break;
-      case 2: k_noalloc_tiles<2, FMT><<<grid, kThreads, 0, s>>>(j, ntiles); break;
-      case 4: k_noalloc_tiles<4, FMT><<<grid, kThreads, 0, s>>>(j, ntiles); break;
-      case 8: k_noalloc_tiles<8, FMT><<<grid, kThreads, 0, s>>>(j, ntiles); break;
-      default: k_noalloc_tiles<16, FMT><<<grid, kThreads, 0, s>>>(j, ntiles); break;
+#define MS_NOALLOC_TILES(PP)                                                      \
+  case PP:                                                                        \
+    if (allow_smem((const void*)k_noalloc_tiles<PP, FMT>, sm) != cudaSuccess)     \
+      return cudaGetLastError();                                                  \
+    k_noalloc_tiles<PP, FMT><<<grid, kThreads, sm, s>>>(j, ntiles);               \
+    break;
+      MS_NOALLOC_TILES(1)
+      MS_NOALLOC_TILES(2)
+      MS_NOALLOC_TILES(4)
+      MS_NOALLOC_TILES(8)
+      default:
+      MS_NOALLOC_TILES(16)
+#undef MS_NOALLOC_TILES
     }
   }
-  k_noalloc_fixup<FMT><<<1, ms::kFixWarps * 32, 0, s>>>(j);
+  const int smf = ms::kFixWarps * ms::kRingWarpBytes;
+  if (allow_smem((const void*)k_noalloc_fixup<FMT>, smf) != cudaSuccess) return cudaGetLastError();
+  k_noalloc_fixup<FMT><<<1, ms::kFixWarps * 32, smf, s>>>(j);
   return cudaGetLastError();
 }
 

@@ -317,3 +317,24 @@ def test_autotune_then_results_unchanged(ctx):
     assert chosen1["packed_path"] in (0, 1)
     assert ctx.max_square(w, n=3000).cpu().tolist() == exp1
     assert ctx.get_tuning()["band_rows"] == 0  # explicit tuning untouched
+
+
+def test_bounded_wait_times_out_and_context_recovers(ctx):
+    """Failure detection without a fault: the first fix-up strip withholds its
+    carries (a test hook), the next strip's wait gives up after about a second,
+    the matrix reports MS_ERR_TIMEOUT and the next call is exact again."""
+    a = gen.bernoulli_u8(700, 2000, 0.6, seed=91)
+    a[100:600, 300:1200] = 1  # a 500-square: the fix-up box spans several strips
+    (K, r, c), _ = oracle.dp(a, want_map=False)
+    x = to_dev(a)
+    ctx.set_tuning(test_hold_carries=1)
+    try:
+        # the dp-map fix-up walks the box in strips that pass carries
+        _, res = ctx.dp_map(x)
+        res = res.cpu().tolist()
+    finally:
+        ctx.set_tuning()
+    assert res[3] == 4  # MS_ERR_TIMEOUT
+    dp, res2 = ctx.dp_map(x)
+    assert res2.cpu().tolist() == [K, r, c, 0]
+    assert ctx.max_square(x).cpu().tolist() == [K, r, c, 0]
