@@ -241,6 +241,7 @@ int64_t tiles_of(const Job& j) { return (int64_t)j.bands * j.strips; }
 // matrices fall back to the strip fix-up.
 int64_t bitfix_words(const Job& j) { return j.m > 0 && j.n > 0 ? 3 * j.m * ((j.n + 31) / 32 + 2) : 0; }
 constexpr int64_t kBitfixCapWords = (int64_t)1 << 30;  // 4 GiB
+constexpr size_t kBitsFixSmemBytes = 200 * 1024;         // planes of small boxes
 
 
 
@@ -336,10 +337,19 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   }
   {
     ProfScope ps(ctx, s, kProfFixup);
-    const size_t sm = ring_bytes(ms::kFixWarps * 32);
-    if (allow_smem((const void*)ms::k_fixup_one<FMT, DPMAP>, sm) != cudaSuccess)
-      return cudaGetLastError();
-    ms::k_fixup_one<FMT, DPMAP><<<1, ms::kFixWarps * 32, sm, s>>>(j);
+    if (!DPMAP && j.bits_scratch) {
+      // size-only: bitplane growth in the flagged box, planes in shared
+      // memory when the box is small enough
+      const size_t sm = kBitsFixSmemBytes;
+      if (allow_smem((const void*)ms::k_fixup_bits_one<FMT>, sm) != cudaSuccess)
+        return cudaGetLastError();
+      ms::k_fixup_bits_one<FMT><<<1, 1024, sm, s>>>(j, (int64_t)(sm / 4));
+    } else {
+      const size_t sm = ring_bytes(ms::kFixWarps * 32);
+      if (allow_smem((const void*)ms::k_fixup_one<FMT, DPMAP>, sm) != cudaSuccess)
+        return cudaGetLastError();
+      ms::k_fixup_one<FMT, DPMAP><<<1, ms::kFixWarps * 32, sm, s>>>(j);
+    }
   }
   return cudaGetLastError();
 }
@@ -498,6 +508,7 @@ __global__ void __launch_bounds__(ms::kFixWarps * 32, 1) k_fixup_mixed(const Job
   const int j = blockIdx.x;
   if (j >= njobs) return;
   const Job job = jobs[j];
+  if (job.bits_scratch) return;  // done by k_fixup_bits_mixed
   if (job.fmt == MS_U8)
     ms::fixup_job<MS_U8, false>(job);
   else
@@ -650,6 +661,7 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   if (bit_need > 0 && grow(ctx, ctx->d_bitfix, ctx->bitfix_cap, bit_need, cap) != MS_OK)
     bit_need = 0;
   int64_t bit_off = 0;
+  bool any_bits = false, any_strip = false;
   for (int32_t i = 0; i < count; ++i) {
     Job& j = jobs[i];
     j.tile0 = 0;
@@ -665,6 +677,7 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
       j.bits_scratch = ctx->d_bitfix + bit_off;
       bit_off += bw;
     }
+    if (j.bits_scratch) any_bits = true; else any_strip = true;
     const int64_t nt = tiles_of(j);
     auto& g = groups[j.fmt * 32 + j.P];
     for (int64_t t = 0; t < nt; ++t) g.push_back(TileRef{i, (int32_t)t, tile_steps(j, t)});
@@ -752,9 +765,17 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   }
   {
     ProfScope ps(ctx, s, kProfFixup);
-    const size_t smf = ring_bytes(ms::kFixWarps * 32);
-    if (allow_smem((const void*)k_fixup_mixed, smf) != cudaSuccess) return MS_ERR_CUDA;
-    k_fixup_mixed<<<count, ms::kFixWarps * 32, smf, s>>>(d_jobs, count);
+    if (any_bits) {
+      const size_t smb = kBitsFixSmemBytes / 2;  // two blocks per SM
+      if (allow_smem((const void*)ms::k_fixup_bits_mixed, smb) != cudaSuccess) return MS_ERR_CUDA;
+      ms::k_fixup_bits_mixed<<<count, ms::kBitsMixedThreads, smb, s>>>(d_jobs, count,
+                                                                      (int64_t)(smb / 4));
+    }
+    if (any_strip) {
+      const size_t smf = ring_bytes(ms::kFixWarps * 32);
+      if (allow_smem((const void*)k_fixup_mixed, smf) != cudaSuccess) return MS_ERR_CUDA;
+      k_fixup_mixed<<<count, ms::kFixWarps * 32, smf, s>>>(d_jobs, count);
+    }
   }
   return cuda_status(cudaGetLastError());
 }

@@ -560,25 +560,65 @@ constexpr int kFixW = 32 * kFixP;  // strip width in the fix-up
 // (doubling from 32, then binary search), and the witness is the first set
 // bit of S_K.  One CTA per matrix; passes are separated by __syncthreads.
 
-struct Plane {  // a bitplane over rows [r0, r1) and words [w0, w1), zero outside
+// A bitplane stored over rows [r0, ...) x words [w0, w0 + pitch) and zero
+// outside its active box [ar0, ar1) x [aw0, aw1), which lies inside the
+// storage.  A plane holds fewer than 2^31 words, so indices fit 32 bits.
+struct Plane {
   uint32_t* p;
-  int64_t r0, r1, w0, w1;
-  __device__ __forceinline__ uint32_t get(int64_t i, int64_t w) const {
-    return (i >= r0 && i < r1 && w >= w0 && w < w1) ? p[(i - r0) * (w1 - w0) + (w - w0)] : 0u;
+  int r0, w0, pitch;
+  int ar0, ar1, aw0, aw1;
+  __device__ __forceinline__ uint32_t get(int i, int w) const {
+    return (i >= ar0 && i < ar1 && w >= aw0 && w < aw1) ? p[(i - r0) * pitch + (w - w0)] : 0u;
   }
+  __device__ __forceinline__ bool empty() const { return ar1 <= ar0 || aw1 <= aw0; }
 };
+
+// Visits the cells (r, c) of a rows x cols grid, spread over the block's
+// threads in row-major order; the row/column step is kept incrementally.
+template <class F>
+__device__ __forceinline__ void for_cells(int rows, int cols, F&& f) {
+  if (rows <= 0 || cols <= 0) return;
+  const int bd = (int)blockDim.x;
+  const int dr = bd / cols, dc = bd - dr * cols;
+  int r = (int)threadIdx.x / cols, c = (int)threadIdx.x - r * cols;
+#pragma unroll 2
+  for (; r < rows;) {
+    f(r, c);
+    r += dr;
+    c += dc;
+    if (c >= cols) {
+      c -= cols;
+      ++r;
+    }
+  }
+}
+
+// bit k of the result = byte k of x is nonzero (k = 0..3): the byte flags
+// sit at bits 0, 8, 16, 24 and one multiply moves them to bits 24..27 without
+// carries (every partial product lands on its own bit).
+__device__ __forceinline__ uint32_t byte_flags4(uint32_t x) {
+  const uint32_t t = (nonzero_msb(x) >> 7) & 0x01010101u;
+  return (t * 0x01020408u) >> 24;
+}
 
 // 32 cells of input row i starting at column 32*w, as bits (columns >= n: 0).
 template <int FMT>
-__device__ __forceinline__ uint32_t input_word(const Job& j, int64_t i, int64_t w) {
-  const int64_t c = 32 * w;
+__device__ __forceinline__ uint32_t input_word(const Job& j, int i, int w) {
+  const int64_t c = 32 * (int64_t)w;
   if (i < 0 || i >= j.m || w < 0 || c >= j.n) return 0u;
   const int64_t valid = j.n - c;
-  const uint32_t mask = valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u);
   if constexpr (FMT == MS_BITS32) {
-    return __ldg(reinterpret_cast<const uint32_t*>(j.data) + i * j.ld + w) & mask;
+    const uint32_t mask = valid >= 32 ? 0xffffffffu : ((1u << valid) - 1u);
+    return __ldg(reinterpret_cast<const uint32_t*>(j.data) + (int64_t)i * j.ld + w) & mask;
   } else {
-    const uint8_t* row = reinterpret_cast<const uint8_t*>(j.data) + i * j.ld + c;
+    const uint8_t* row = reinterpret_cast<const uint8_t*>(j.data) + (int64_t)i * j.ld + c;
+    if (valid >= 32 && j.aligned) {
+      const uint4 lo = __ldg(reinterpret_cast<const uint4*>(row));
+      const uint4 hi = __ldg(reinterpret_cast<const uint4*>(row) + 1);
+      return byte_flags4(lo.x) | byte_flags4(lo.y) << 4 | byte_flags4(lo.z) << 8 |
+             byte_flags4(lo.w) << 12 | byte_flags4(hi.x) << 16 | byte_flags4(hi.y) << 20 |
+             byte_flags4(hi.z) << 24 | byte_flags4(hi.w) << 28;
+    }
     uint32_t bits = 0;
     const int lim = valid >= 32 ? 32 : (int)valid;
     for (int b = 0; b < lim; ++b) bits |= (uint32_t)(__ldg(row + b) != 0) << b;
@@ -586,137 +626,247 @@ __device__ __forceinline__ uint32_t input_word(const Job& j, int64_t i, int64_t 
   }
 }
 
-// out = grow(L, d) on plane O (rows/words of O), returns whether any bit is set.
-__device__ __forceinline__ bool grow_pass(const Plane& L, const Plane& O, int64_t d, int64_t n,
-                                          bool write, unsigned long long* first) {
-  const int q = (int)(d >> 5), r = (int)(d & 31);
-  const int64_t W = O.w1 - O.w0, total = (O.r1 - O.r0) * W;
-  bool any = false;
+// Per-pass bounding box of the nonzero words a block writes.  Threads reduce
+// per warp and fold into slot k % 3 with shared-memory atomics; slot
+// (k+1) % 3 is reset during pass k (its last readers finished before the
+// barrier of pass k-1), so each pass needs a single __syncthreads.
+struct PassBox {
+  int (*slot)[4];  // shared [3][4]: row min, row max, word min, word max
+  int k;
+  __device__ __forceinline__ void begin() const {
+    if (threadIdx.x == 0) {
+      int* b = slot[(k + 1) % 3];
+      b[0] = 0x7fffffff;
+      b[1] = -1;
+      b[2] = 0x7fffffff;
+      b[3] = -1;
+    }
+  }
+  // all threads; returns [r0, r1) x [w0, w1) (empty: r1 <= r0)
+  __device__ __forceinline__ void end(int rmin, int rmax, int wmin, int wmax, int out[4]) {
+    rmin = __reduce_min_sync(0xffffffffu, rmin);
+    rmax = __reduce_max_sync(0xffffffffu, rmax);
+    wmin = __reduce_min_sync(0xffffffffu, wmin);
+    wmax = __reduce_max_sync(0xffffffffu, wmax);
+    int* b = slot[k % 3];
+    if ((threadIdx.x & 31) == 0 && rmax >= 0) {
+      atomicMin(b + 0, rmin);
+      atomicMax(b + 1, rmax);
+      atomicMin(b + 2, wmin);
+      atomicMax(b + 3, wmax);
+    }
+    __syncthreads();
+    out[0] = b[0];
+    out[1] = b[1] + 1;
+    out[2] = b[2];
+    out[3] = b[3] + 1;
+    ++k;
+  }
+};
+
+// O = grow(L, d) = S_{a+d} from L = S_a (0 <= d <= a): bit (i, col) is
+// L(i, col) & L(i-d, col) & L(i, col-d) & L(i-d, col-d), columns >= n cleared.
+// Only L's active box (clipped to O's storage rows/words) can be nonzero.
+// Writes O's words there (if write) and sets O's active box; `first`
+// receives the smallest row-major index of a set bit.
+__device__ __forceinline__ void grow_pass(const Plane& L, Plane& O, int o_r1, int o_w1, int d,
+                                          int64_t n, bool write, unsigned long long* first,
+                                          PassBox& pb) {
+  const int q = d >> 5, r = d & 31;
+  const int r0 = max(L.ar0, O.r0), r1 = min(L.ar1, o_r1);
+  const int w0 = max(L.aw0, O.w0), w1 = min(L.aw1, o_w1);
+  int rmin = 0x7fffffff, rmax = -1, wmin = 0x7fffffff, wmax = -1;
   unsigned long long f = ~0ull;
-#pragma unroll 4
-  for (int64_t e = threadIdx.x; e < total; e += blockDim.x) {
-    const int64_t i = O.r0 + e / W, w = O.w0 + e % W;
+  pb.begin();
+  for_cells(r1 - r0, w1 - w0, [&](int rr, int cc) {
+    const int i = r0 + rr, w = w0 + cc;
     const uint32_t a0 = L.get(i, w), a1 = L.get(i - d, w);
     uint32_t a2 = L.get(i, w - q), a3 = L.get(i - d, w - q);
     if (r) {
       a2 = (a2 << r) | (L.get(i, w - q - 1) >> (32 - r));
       a3 = (a3 << r) | (L.get(i - d, w - q - 1) >> (32 - r));
     }
-    const int64_t valid = n - 32 * w;
+    const int64_t valid = n - 32 * (int64_t)w;
     const uint32_t cm = valid >= 32 ? 0xffffffffu : (valid <= 0 ? 0u : ((1u << valid) - 1u));
     const uint32_t v = a0 & a1 & a2 & a3 & cm;
-    if (write) O.p[e] = v;
+    if (write) O.p[(i - O.r0) * O.pitch + (w - O.w0)] = v;
     if (v) {
-      any = true;
+      rmin = min(rmin, i);
+      rmax = max(rmax, i);
+      wmin = min(wmin, w);
+      wmax = max(wmax, w);
       if (first) {
-        const unsigned long long cand =
-            (unsigned long long)i * (unsigned long long)n + (unsigned long long)(32 * w) +
-            (unsigned long long)(__ffs(v) - 1);
+        const unsigned long long cand = (unsigned long long)i * (unsigned long long)n +
+                                        (unsigned long long)(32 * (int64_t)w) +
+                                        (unsigned long long)(__ffs(v) - 1);
         f = cand < f ? cand : f;
       }
     }
-  }
+  });
   if (first && f != ~0ull) atomicMin(first, f);
-  return __syncthreads_or(any ? 1 : 0) != 0;
+  int box[4];
+  pb.end(rmin, rmax, wmin, wmax, box);
+  O.ar0 = box[0];
+  O.ar1 = box[1];
+  O.aw0 = box[2];
+  O.aw1 = box[3];
 }
 
+// The three planes live in shared memory when they fit in `smem_words`
+// words (small boxes: every pass then runs from shared memory), else in the
+// job's global scratch.
 template <int FMT>
-__device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int clo, int chi) {
+__device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int clo, int chi,
+                                           uint32_t* smem, int64_t smem_words) {
   __shared__ unsigned long long s_first;
-  const int64_t ra = max(0, rlo - kHalo);
-  const int64_t wlo = clo / 32, whi = (chi + 31) / 32;
-  const int64_t wa = max(0, clo - kHalo) / 32;
-  const int64_t R1 = rhi - ra, W1 = whi - wa;
-  const int64_t cap = j.m * ((j.n + 31) / 32 + 2);
-  uint32_t* buf0 = j.bits_scratch;            // V_32 (vertical runs >= 32), then levels
-  uint32_t* buf1 = j.bits_scratch + cap;      // S_32 on the grown box
-  uint32_t* buf2 = j.bits_scratch + 2 * cap;  // packed input, then levels
+  __shared__ int s_box[3][4];
+  PassBox pb{s_box, 0};
+  if (threadIdx.x == 0) {
+    s_box[0][0] = 0x7fffffff;
+    s_box[0][1] = -1;
+    s_box[0][2] = 0x7fffffff;
+    s_box[0][3] = -1;
+    s_first = ~0ull;
+  }
+  const int ra = max(0, rlo - kHalo);
+  const int wlo = clo / 32, whi = (chi + 31) / 32;
+  const int wa = max(0, clo - kHalo) / 32;
+  const int R1 = rhi - ra, W1 = whi - wa;
+  const int pa = max(0, ra - 31);
+  const int Wv = W1 + 1, RP = rhi - pa;
+  uint32_t *buf0, *buf1, *buf2;  // V_32 then levels / S_32 on the grown box / input then levels
+  if (smem && 2 * (int64_t)RP * Wv + (int64_t)R1 * W1 <= smem_words) {
+    buf2 = smem;
+    buf0 = smem + RP * Wv;
+    buf1 = smem + 2 * RP * Wv;
+  } else {
+    const int64_t cap = j.m * ((j.n + 31) / 32 + 2);
+    buf0 = j.bits_scratch;
+    buf1 = j.bits_scratch + cap;
+    buf2 = j.bits_scratch + 2 * cap;
+  }
   // 1. input bits of rows [pa, rhi), words [wa-1, whi)
-  const int64_t pa = max((int64_t)0, ra - 31);
-  const int64_t Wv = W1 + 1, RP = rhi - pa;
-#pragma unroll 4
-  for (int64_t e = threadIdx.x; e < RP * Wv; e += blockDim.x)
-    buf2[e] = input_word<FMT>(j, pa + e / Wv, wa - 1 + e % Wv);
+  for_cells(RP, Wv, [&](int rr, int cc) {
+    buf2[rr * Wv + cc] = input_word<FMT>(j, pa + rr, wa - 1 + cc);
+  });
   __syncthreads();
   // 2. vertical: V_32(i, w) = AND of the 32 rows ending at i, by doubling
   //    V_2k(i) = V_k(i) & V_k(i-k) over rows [pa, rhi) (5 passes, ping-pong
-  //    between buf2 and buf0).  Rows above pa read as zeros, so V_k is exact
-  //    on rows >= pa + k - 1, which covers every row >= ra (pa = ra - 31, or
-  //    pa = 0 at the matrix top where the zeros are real).
+  //    between buf2 and buf0, ending in buf0).  Rows above pa read as zeros,
+  //    so V_k is exact on rows >= pa + k - 1, which covers every row >= ra
+  //    (pa = ra - 31, or pa = 0 at the matrix top where the zeros are real).
   {
     uint32_t* src = buf2;
     uint32_t* dst = buf0;
     for (int k = 1; k < 32; k *= 2) {
-#pragma unroll 4
-      for (int64_t e = threadIdx.x; e < RP * Wv; e += blockDim.x) {
-        const int64_t i = pa + e / Wv;
-        const uint32_t up = (i - k >= pa) ? src[e - (int64_t)k * Wv] : 0u;
-        dst[e] = src[e] & up;
-      }
+      for_cells(RP, Wv, [&](int rr, int cc) {
+        const int e = rr * Wv + cc;
+        dst[e] = rr >= k ? src[e] & src[e - k * Wv] : 0u;
+      });
       __syncthreads();
       uint32_t* t = src;
       src = dst;
       dst = t;
     }
-    if (src != buf0)
-      for (int64_t e = threadIdx.x; e < RP * Wv; e += blockDim.x) buf0[e] = src[e];
-    __syncthreads();
   }
-  // 3. horizontal: S_32 = AND of 32 consecutive V_32 bits ending at each cell
-  for (int64_t e = threadIdx.x; e < R1 * W1; e += blockDim.x) {
-    const int64_t ii = e / W1, col = e % W1;
-    const int64_t vr = ii + (ra - pa);  // row of V_32 in its [pa, rhi) layout
-    const uint32_t x = buf0[vr * Wv + col + 1], y = buf0[vr * Wv + col];
-    unsigned long long z = ((unsigned long long)x << 32) | y;
-    z &= z << 1;
-    z &= z << 2;
-    z &= z << 4;
-    z &= z << 8;
-    z &= z << 16;
-    buf1[e] = (uint32_t)(z >> 32);
+  // 3. horizontal: S_32 = AND of 32 consecutive V_32 bits ending at each
+  //    cell, on rows [ra, rhi) x words [wa, whi)
+  Plane s32{buf1, ra, wa, W1, 0, 0, 0, 0};
+  {
+    int rmin = 0x7fffffff, rmax = -1, wmin = 0x7fffffff, wmax = -1;
+    pb.begin();
+    for_cells(R1, W1, [&](int rr, int cc) {
+      const int vr = rr + (ra - pa);  // row of V_32 in its [pa, rhi) layout
+      const uint32_t x = buf0[vr * Wv + cc + 1], y = buf0[vr * Wv + cc];
+      unsigned long long z = ((unsigned long long)x << 32) | y;
+      z &= z << 1;
+      z &= z << 2;
+      z &= z << 4;
+      z &= z << 8;
+      z &= z << 16;
+      const uint32_t v = (uint32_t)(z >> 32);
+      buf1[rr * W1 + cc] = v;
+      if (v) {
+        rmin = min(rmin, ra + rr);
+        rmax = max(rmax, ra + rr);
+        wmin = min(wmin, wa + cc);
+        wmax = max(wmax, wa + cc);
+      }
+    });
+    int box[4];
+    pb.end(rmin, rmax, wmin, wmax, box);
+    s32.ar0 = box[0];
+    s32.ar1 = box[1];
+    s32.aw0 = box[2];
+    s32.aw1 = box[3];
   }
-  __syncthreads();
-  const Plane s32{buf1, ra, rhi, wa, whi};
-  // 3. doubling from 32 inside the box, then binary search
-  const Plane box0{buf0, rlo, rhi, wlo, whi}, box2{buf2, rlo, rhi, wlo, whi};
-  Plane cur = s32, nxt = box0;
-  int64_t a = 32, lo, hi;
-  const int64_t kmax = min(j.m, j.n);
+  // 4. doubling from 32 inside the box [rlo, rhi) x [wlo, whi), then binary
+  //    search; level planes alternate between buf0 and buf2
+  const int BW = whi - wlo;
+  Plane cur = s32, nxt{buf0, rlo, wlo, BW, 0, 0, 0, 0};
+  uint32_t* spare = buf2;
+  int a = 32, lo, hi;
+  const int kmax = (int)min(j.m, j.n);
   for (;;) {
-    if (2 * a > kmax) {
+    if (2 * a > kmax || cur.empty()) {
       lo = a;
-      hi = kmax + 1;
+      hi = min(2 * a, kmax + 1);
       break;
     }
-    const bool ne = grow_pass(cur, nxt, a, j.n, true, nullptr);
-    __syncthreads();
-    if (!ne) {
+    grow_pass(cur, nxt, rhi, whi, a, j.n, true, nullptr, pb);
+    if (nxt.empty()) {
       lo = a;
       hi = 2 * a;
       break;
     }
     a *= 2;
-    const Plane done = cur;
+    uint32_t* freed = cur.p == buf1 ? spare : cur.p;
     cur = nxt;
-    nxt = (done.p == buf1) ? box2 : done;
+    nxt = Plane{freed, rlo, wlo, BW, 0, 0, 0, 0};
   }
+  Plane probe = nxt;  // tests write nothing
   while (hi - lo > 1) {
-    const int64_t t = (lo + hi) / 2;
-    const bool ne = grow_pass(cur, box0, t - a, j.n, false, nullptr);
-    if (ne) lo = t; else hi = t;
+    const int t = (lo + hi) / 2;
+    grow_pass(cur, probe, rhi, whi, t - a, j.n, false, nullptr, pb);
+    if (!probe.empty()) lo = t; else hi = t;
   }
-  // 4. witness: the first set bit of S_lo inside the box
-  if (threadIdx.x == 0) s_first = ~0ull;
-  __syncthreads();
-  const Plane wbox{nullptr, rlo, rhi, wlo, whi};
-  grow_pass(cur, wbox, lo - a, j.n, false, &s_first);
-  __syncthreads();
+  // 5. witness: the first set bit of S_lo inside the box
+  grow_pass(cur, probe, rhi, whi, lo - a, j.n, false, &s_first, pb);
   if (threadIdx.x == 0 && s_first != ~0ull) {
     const unsigned long long idx = s_first;
     atomicMax(&j.st->key, make_key((int32_t)lo, (int64_t)(idx / (unsigned long long)j.n),
                                    (int64_t)(idx % (unsigned long long)j.n), j.n));
   }
   __syncthreads();
+}
+
+// Writes the matrix's result from its key and leaves its state ready for the
+// next call (call after a __syncthreads that follows all updates of the key).
+__device__ __forceinline__ void finalize_job(const Job& j) {
+  JobState* st = j.st;
+  if (threadIdx.x == 0) {
+    const unsigned long long key = ld_volatile_u64(&st->key);
+    ms_result r;
+    r.status = *reinterpret_cast<volatile int32_t*>(&st->status);
+    if (key == 0ull) {
+      r.side = 0;
+      r.row = -1;
+      r.col = -1;
+    } else {
+      const unsigned long long idx = kKeyMask - (key & kKeyMask);
+      r.side = (int32_t)(key >> 40);
+      r.row = (int32_t)(idx / (unsigned long long)j.n);
+      r.col = (int32_t)(idx % (unsigned long long)j.n);
+    }
+    *j.out = r;
+    // leave the state ready for the next call
+    st->key = 0ull;
+    st->box[0] = 0x7fffffff;
+    st->box[1] = -1;
+    st->box[2] = 0x7fffffff;
+    st->box[3] = -1;
+    st->status = 0;
+  }
 }
 
 template <int FMT, bool DPMAP>
@@ -731,9 +881,7 @@ __device__ __forceinline__ void fixup_job(const Job& j) {
   }
   __syncthreads();
   const int rlo = sbox[0], rhi = sbox[1], clo = sbox[2], chi = sbox[3];
-  if (!DPMAP && j.bits_scratch && rhi > rlo && chi > clo) {
-    fixup_bits<FMT>(j, rlo, rhi, clo, chi);
-  } else if (rhi > rlo && chi > clo) {
+  if (rhi > rlo && chi > clo) {
     const int64_t br0 = max(0, rlo - kHalo);
     // rounded down to 32 columns: fix-up chunks must stay inside a packed
     // word and keep vector loads aligned (a wider window is still exact)
@@ -771,29 +919,46 @@ __device__ __forceinline__ void fixup_job(const Job& j) {
     for (int s = threadIdx.x; s < nstrips && s < j.strips_fix; s += blockDim.x) j.progress[s] = 0;
   }
   __syncthreads();
+  finalize_job(j);
+}
+
+// Size-only fix-up of one matrix by bitplane growth, then its result.
+template <int FMT>
+__device__ __forceinline__ void fixup_bits_job(const Job& j, uint32_t* smem, int64_t smem_words) {
+  __shared__ int32_t sbox[4];
   if (threadIdx.x == 0) {
-    const unsigned long long key = ld_volatile_u64(&st->key);
-    ms_result r;
-    r.status = *reinterpret_cast<volatile int32_t*>(&st->status);
-    if (key == 0ull) {
-      r.side = 0;
-      r.row = -1;
-      r.col = -1;
-    } else {
-      const unsigned long long idx = kKeyMask - (key & kKeyMask);
-      r.side = (int32_t)(key >> 40);
-      r.row = (int32_t)(idx / (unsigned long long)j.n);
-      r.col = (int32_t)(idx % (unsigned long long)j.n);
-    }
-    *j.out = r;
-    // leave the state ready for the next call
-    st->key = 0ull;
-    st->box[0] = 0x7fffffff;
-    st->box[1] = -1;
-    st->box[2] = 0x7fffffff;
-    st->box[3] = -1;
-    st->status = 0;
+    sbox[0] = j.st->box[0];
+    sbox[1] = j.st->box[1];
+    sbox[2] = j.st->box[2];
+    sbox[3] = j.st->box[3];
   }
+  __syncthreads();
+  if (sbox[1] > sbox[0] && sbox[3] > sbox[2])
+    fixup_bits<FMT>(j, sbox[0], sbox[1], sbox[2], sbox[3], smem, smem_words);
+  __syncthreads();
+  finalize_job(j);
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(1024, 1) k_fixup_bits_one(const Job job, int64_t smem_words) {
+  extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
+  fixup_bits_job<FMT>(job, reinterpret_cast<uint32_t*>(ms_dyn_smem), smem_words);
+}
+
+// Batch: every job with bitplane scratch (the others go to the strip fix-up).
+constexpr int kBitsMixedThreads = 512;
+static __global__ void __launch_bounds__(kBitsMixedThreads, 2)
+    k_fixup_bits_mixed(const Job* __restrict__ jobs, int njobs, int64_t smem_words) {
+  extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
+  const int jj = blockIdx.x;
+  if (jj >= njobs) return;
+  const Job job = jobs[jj];
+  if (!job.bits_scratch) return;
+  uint32_t* smem = reinterpret_cast<uint32_t*>(ms_dyn_smem);
+  if (job.fmt == MS_U8)
+    fixup_bits_job<MS_U8>(job, smem, smem_words);
+  else
+    fixup_bits_job<MS_BITS32>(job, smem, smem_words);
 }
 
 template <int FMT, bool DPMAP>
