@@ -471,7 +471,7 @@ def run_ours(args, world, rank, local, pg):
     packed_path = args.packed_path
     if packed_path is None:
         packed_path = 1 if ("bits" in args.workload and not args.workload.endswith("-dp")) else 0
-    ctx.set_tuning(packed_path=packed_path)
+    ctx.set_tuning(packed_path=packed_path, band_rows=args.band_rows, lane_cols=args.lane_cols)
     wl = make_workload(args.workload, device, host=True)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -613,6 +613,8 @@ def run_ours(args, world, rank, local, pg):
                 "dtype": wl.dtype, "data": "synthetic (seeded SplitMix64 Bernoulli matrices)",
                 "config": {**wl.config(), "parallelism": f"replicas x{world}",
                            "packed_path": packed_path,
+                           **({"band_rows": args.band_rows} if args.band_rows else {}),
+                           **({"lane_cols": args.lane_cols} if args.lane_cols else {}),
                            "timed_path": ("ms_batch, CUDA graph replay" if batch_headline
                                           else "one ms_* call per matrix (plain)")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
@@ -745,6 +747,10 @@ def main():
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--packed-path", type=int, default=None,
                     help="1: bitplane search for packed size-only work (default for c3-bits)")
+    ap.add_argument("--band-rows", type=int, default=0,
+                    help="rows per tile (0: automatic, or autotuned for multi-matrix runs)")
+    ap.add_argument("--lane-cols", type=int, default=0,
+                    help="columns per lane in a tile (0: automatic)")
     args = ap.parse_args()
     world, rank, local, pg = dist_setup(args)
     try:

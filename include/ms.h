@@ -116,7 +116,7 @@ ms_status ms_destroy(ms_ctx* ctx);
  * device.  Such callers cannot create an ms_ctx, so this call needs none and
  * allocates nothing: it computes the same result as ms_max_square into
  * out_dev (one ms_result in device memory), using a fixed scratch array of
- * about 1.1 MiB that lives in the library's device image on every GPU that
+ * about 0.53 MiB that lives in the library's device image on every GPU that
  * loads the library, until the process exits.
  * - Limits: m <= 8192 and n <= 8192 (MS_U8 or MS_BITS32); a larger matrix
  *   returns MS_ERR_UNSUPPORTED and launches nothing.
@@ -187,7 +187,9 @@ double ms_server_now(void);
  * (each tile also re-reads a halo of 32 rows above and 32 columns to its
  * left), `packed_path` selects, for MS_BITS32 size-only work, the bitplane
  * erosion search (1) or the byte-style tile kernel on unpacked bits (0).
- * 0 for band_rows = choose automatically from the matrix size. */
+ * `lane_cols` = columns each lane of a warp owns in a tile (1, 2, 4, 8, 16
+ * or 32; a tile is 32 * lane_cols columns wide).
+ * 0 for band_rows or lane_cols = choose automatically from the matrix size. */
 typedef struct {
   int32_t band_rows;
   int32_t packed_path;
@@ -196,7 +198,8 @@ typedef struct {
    * bounded wait (about 1 s) runs out and the matrix's ms_result.status is
    * MS_ERR_TIMEOUT; later calls with the hook off are unaffected. */
   int32_t test_hold_carries;
-  int32_t reserved[5];
+  int32_t lane_cols;
+  int32_t reserved[4];
 } ms_tuning;
 
 ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t);
@@ -205,11 +208,12 @@ ms_status ms_get_tuning(ms_ctx* ctx, ms_tuning* t);
 /* Autotuner (a library feature; the paper has no counterpart).  Times the
  * work of ms_max_square (count == 1) or ms_batch (count > 1) on the given
  * matrices for each candidate tuning -- band heights 32..1024 and the
- * automatic choice, and for MS_BITS32 size-only work both packed paths --
+ * automatic choice, lane widths 16, 32 and the automatic choice, and for
+ * MS_BITS32 size-only work both packed paths --
  * keeps the fastest, and caches it in the context under the workload's class
  * (entry point, format mix, log2 of the cell count, log2 of the matrix
- * count).  Later calls of that class with ms_tuning.band_rows == 0 use the
- * cached choice.  `outs_dev` receives results (count entries) and is
+ * count).  Later calls of that class with ms_tuning.band_rows == 0 and
+ * lane_cols == 0 use the cached choice.  `outs_dev` receives results (count entries) and is
  * scratch.  Blocks the calling thread until the timing runs finish; must
  * not be called during stream capture.  The chosen tuning is written to
  * `chosen` if non-null. */

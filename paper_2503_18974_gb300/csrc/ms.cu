@@ -18,6 +18,7 @@ using ms::JobState;
 
 struct ms_ctx {
   int device = 0;
+  int sms = 1;        // streaming multiprocessors of the device
   size_t budget = 0;  // 0 = unlimited
   size_t held = 0;    // bytes of device workspace currently held
   ms_tuning tuning{};
@@ -139,12 +140,20 @@ bool capturing(cudaStream_t s) {
   return cs != cudaStreamCaptureStatusNone;
 }
 
-int choose_P(int64_t n) {
+// Columns per lane.  Very large size-only matrices take 32 (fewer
+// instructions and halo columns per cell, and still enough tiles to fill the
+// GPU); narrow ones take the narrowest tile covering them; the rest, and the
+// dp map (its stores keep more values live), take 16.  A 32-column tile has
+// no room for a second strip, so lane width 1 only serves n <= 32.
+int choose_P(int64_t m, int64_t n, bool dp, int32_t forced) {
+  if (forced > 1 || (forced == 1 && n <= 32)) return forced;
+  if (forced == 1) return 2;
   if (n <= 32) return 1;
   if (n <= 64) return 2;
   if (n <= 128) return 4;
   if (n <= 256) return 8;
-  return 16;
+  if (dp || m * n < ((int64_t)1 << 29)) return 16;
+  return 32;
 }
 
 int64_t strips_for(int64_t n, int P) {
@@ -188,10 +197,12 @@ uint64_t tune_class(const ms_matrix* ins, int64_t count, bool batch) {
          (uint64_t)lk;
 }
 
-// The tuning a call uses: explicit band_rows from ms_set_tuning wins, else a
+// The tuning a call uses: an explicit band_rows or lane_cols from
+// ms_set_tuning wins, else a
 // cached autotune result for the class, else the context's tuning (automatic).
 ms_tuning effective_tuning(const ms_ctx* ctx, const ms_matrix* ins, int64_t count, bool batch) {
-  if (ctx->tuning.band_rows > 0 || ctx->tuned.empty()) return ctx->tuning;
+  if (ctx->tuning.band_rows > 0 || ctx->tuning.lane_cols > 0 || ctx->tuned.empty())
+    return ctx->tuning;
   auto it = ctx->tuned.find(tune_class(ins, count, batch));
   return it == ctx->tuned.end() ? ctx->tuning : it->second;
 }
@@ -212,7 +223,7 @@ ms_status check_matrix(const ms_matrix* in) {
   return MS_OK;
 }
 
-Job plan_job(const ms_tuning& tune, const ms_matrix* in) {
+Job plan_job(const ms_tuning& tune, const ms_matrix* in, bool dp, int max_P = 32) {
   Job j;
   std::memset(&j, 0, sizeof(j));
   j.data = in->data;
@@ -220,7 +231,7 @@ Job plan_job(const ms_tuning& tune, const ms_matrix* in) {
   j.n = in->n;
   j.ld = in->ld;
   j.fmt = in->fmt;
-  j.P = choose_P(in->n);
+  j.P = std::min(choose_P(in->m, in->n, dp, tune.lane_cols), max_P);
   if (in->m > 0 && in->n > 0) {
     j.strips = (int32_t)strips_for(in->n, j.P);
     j.band_rows = tune.band_rows > 0 ? (int32_t)std::min<int64_t>(tune.band_rows, in->m)
@@ -316,22 +327,26 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   if (ntiles > 0) {
     ProfScope ps(ctx, s, kProfTile);
     const int64_t warps = (ntiles + 1) / 2;
-    const int wpb = kTileThreads / 32;
+    // small launches spread their warps over all SMs (one block per SM at
+    // most): a lone tile is latency-bound, and packing its warps onto a few
+    // SMs would make them share those SMs' ALU pipes
+    const int wpb = (int)std::min<int64_t>(kTileThreads / 32, (warps + ctx->sms - 1) / ctx->sms);
     const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
-    const size_t sm = ring_bytes(kTileThreads);
+    const size_t sm = ring_bytes(32 * wpb);
     switch (j.P) {
 #define MS_LAUNCH_TILES(PP)                                                             \
   case PP:                                                                              \
     if (allow_smem((const void*)ms::k_tiles_one<PP, FMT, DPMAP>, sm) != cudaSuccess)    \
       return cudaGetLastError();                                                        \
-    ms::k_tiles_one<PP, FMT, DPMAP><<<grid, kTileThreads, sm, s>>>(j, ntiles);          \
+    ms::k_tiles_one<PP, FMT, DPMAP><<<grid, 32 * wpb, sm, s>>>(j, ntiles);              \
     break;
       MS_LAUNCH_TILES(1)
       MS_LAUNCH_TILES(2)
       MS_LAUNCH_TILES(4)
       MS_LAUNCH_TILES(8)
-      default:
       MS_LAUNCH_TILES(16)
+      default:
+      MS_LAUNCH_TILES(32)
 #undef MS_LAUNCH_TILES
     }
   }
@@ -480,8 +495,8 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   DeviceGuard g(ctx->device);
   const ms_tuning tune = effective_tuning(ctx, in, 1, false);
   if (!dp && bits_search_applies(tune, in)) return run_bits_search(ctx, in, out_dev, s);
-  Job j = plan_job(tune, in);
-  st = ensure_workspace(ctx, 1, j.m * (int64_t)j.strips_fix, j.strips_fix, s);
+  Job j = plan_job(tune, in, dp != nullptr);
+  st = ensure_workspace(ctx, 1, ms::carry_words(j.m, j.strips_fix), j.strips_fix, s);
   if (st != MS_OK) return st;
   const int64_t bw = dp ? 0 : bitfix_words(j);
   if (bw > 0 && bw <= kBitfixCapWords &&
@@ -554,10 +569,14 @@ ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes) {
   ctx->device = device;
   ctx->budget = workspace_budget_bytes;
   DeviceGuard g(device);
-  if (cudaEventCreateWithFlags(&ctx->stage_free, cudaEventDisableTiming) != cudaSuccess) {
+  if (cudaEventCreateWithFlags(&ctx->stage_free, cudaEventDisableTiming) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
     delete ctx;
     return MS_ERR_CUDA;
   }
+  ctx->sms = std::max(ctx->sms, 1);
   ms_status st = ensure_workspace(ctx, 64, 1 << 16, 1024, nullptr);
   if (st != MS_OK) {
     ms_destroy(ctx);
@@ -596,6 +615,9 @@ ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t) {
   if (t->band_rows < 0 || t->band_rows > 65000) return MS_ERR_INVALID;
   if (t->packed_path < 0 || t->packed_path > 1) return MS_ERR_INVALID;
   if (t->test_hold_carries < 0 || t->test_hold_carries > 1) return MS_ERR_INVALID;
+  if (t->lane_cols != 0 && t->lane_cols != 1 && t->lane_cols != 2 && t->lane_cols != 4 &&
+      t->lane_cols != 8 && t->lane_cols != 16 && t->lane_cols != 32)
+    return MS_ERR_INVALID;
   ctx->tuning = *t;
   return MS_OK;
 }
@@ -636,8 +658,8 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   std::vector<Job> jobs((size_t)count);
   int64_t carry = 0, progress = 0, work = 0;
   for (int32_t i = 0; i < count; ++i) {
-    jobs[i] = plan_job(tune, &ins_host[i]);
-    carry += jobs[i].m * (int64_t)jobs[i].strips_fix;
+    jobs[i] = plan_job(tune, &ins_host[i], false, 16);  // the batch kernel: P <= 16
+    carry += ms::carry_words(jobs[i].m, jobs[i].strips_fix);
     progress += jobs[i].strips_fix;
     work += jobs[i].m * (int64_t)jobs[i].strips;
   }
@@ -654,7 +676,7 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   // tiles of one format and lane width pair up in a warp; pairs of similar
   // length, longest first, form the queue of the persistent launch
   struct TileRef { int32_t job, tile, steps; };
-  std::vector<std::vector<TileRef>> groups(2 * 32);
+  std::vector<std::vector<TileRef>> groups(2 * 64);
   int64_t carry_off = 0, prog_off = 0, bit_need = 0;
   for (int32_t i = 0; i < count; ++i) bit_need += bitfix_words(jobs[i]);
   bit_need = std::min(bit_need, kBitfixCapWords);
@@ -669,7 +691,7 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     j.st = ctx->d_states + i;
     j.carry = ctx->d_carry + carry_off;
     j.progress = ctx->d_progress + prog_off;
-    carry_off += j.m * (int64_t)j.strips_fix;
+    carry_off += ms::carry_words(j.m, j.strips_fix);
     prog_off += j.strips_fix;
     const int64_t bw = bitfix_words(j);
     j.bits_scratch = nullptr;
@@ -679,7 +701,7 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     }
     if (j.bits_scratch) any_bits = true; else any_strip = true;
     const int64_t nt = tiles_of(j);
-    auto& g = groups[j.fmt * 32 + j.P];
+    auto& g = groups[j.fmt * 64 + j.P];
     for (int64_t t = 0; t < nt; ++t) g.push_back(TileRef{i, (int32_t)t, tile_steps(j, t)});
   }
   std::vector<ms::PairTask> tasks;
@@ -794,14 +816,20 @@ ms_status ms_autotune(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_
   const bool packed_single = !batch && ins_host[0].fmt == MS_BITS32;
   std::vector<ms_tuning> cands;
   const int rows[] = {0, 32, 64, 128, 256, 512, 1024};
+  const int lanes[] = {0, 16, 32};
   for (int pp = 0; pp <= (packed_single ? 1 : 0); ++pp)
-    for (int r : rows) {
-      if (pp == 1 && r != 0) continue;  // the bitplane search has no band height
-      ms_tuning t{};
-      t.band_rows = r;
-      t.packed_path = pp;
-      cands.push_back(t);
-    }
+    for (int lc : lanes)
+      for (int r : rows) {
+        // the bitplane search has no band height or lane width; batches use
+        // the automatic lane width (at most 16)
+        if (pp == 1 && (r != 0 || lc != 0)) continue;
+        if (batch && lc != 0) continue;
+        ms_tuning t{};
+        t.band_rows = r;
+        t.packed_path = pp;
+        t.lane_cols = lc;
+        cands.push_back(t);
+      }
   const ms_tuning saved = ctx->tuning;
   const auto saved_cache = ctx->tuned;
   ctx->tuned.clear();

@@ -5,16 +5,16 @@
 // the first cell reaching it in row-major order (where the paper's
 // Algorithm 1, Sec. 3.2, makes its last validation).
 //
-// Restatement used on the GPU.  With h = vertical run of ones ending at the
-// cell (the paper's frequency array freq[j], Sec. 3.4) and left = horizontal
-// run ending at the cell (the paper's counter when the threshold is 1),
-//   dp[i][j] = min(dp[i-1][j-1] + 1, h[i][j], left[i][j]).
-// In row units, A = i + 1 - dp, Z = i + 1 - h (one past the last zero row of
-// the column) and Q = i + 1 - left turn the three-way minimum into
-//   A[i][j] = max(A[i-1][j-1], Z[i][j], Q[i][j]),
-// where Z only changes at a zero cell (Z := i + 1) and Q is a chain along the
-// row (Q := Q_left - 1 on a one, i + 1 on a zero).  All three quantities are
-// small non-negative integers kept two per 32-bit register (16x2 SIMD).
+// Restatement used on the GPU.  Eq. 1 on a one cell is
+//   dp[i][j] = 1 + min(dp[i-1][j], dp[i][j-1], dp[i-1][j-1]),
+// and 0 on a zero cell.  In row units A = i + 1 - dp (one past the last row
+// the square does not cover) the minimum becomes a maximum:
+//   A[i][j] = max(A[i-1][j], A[i-1][j-1], A[i][j-1] - 1)  on a one,
+//   A[i][j] = i + 1                                        on a zero,
+// because the row index of the neighbours above is one less.  The paper's
+// frequency array (the vertical run h, Sec. 3.4) is implicit: A >= i + 1 - h.
+// A is a small non-negative integer; two independent tiles share every 32-bit
+// register (16x2 SIMD), so one max.u16x2 serves two cells.
 #pragma once
 #include <cstdint>
 
@@ -53,12 +53,19 @@ struct Job {
   int32_t pad;
   ms_result* out;
   JobState* st;
-  uint32_t* carry;         // fix-up strip carries: strips_fix rows each
+  uint32_t* carry;         // fix-up strip carries (carry_words(m, strips_fix) words, 16-B aligned)
   int32_t* progress;       // fix-up per-strip published row counts
   int32_t strips_fix;      // capacity of carry/progress in strips
   int32_t test_hold;       // test hook: the first fix-up strip never publishes carries
   uint32_t* bits_scratch;  // size-only fix-up bitplanes (3 x m x (ceil(n/32)+2) words), or null
 };
+
+// Fix-up strip carries: one uint16 per window row and strip, each strip's
+// rows padded to a multiple of 8 so that 8 rows load as one 16-byte vector.
+__host__ __device__ constexpr int64_t carry_stride16(int64_t m) { return (m + 7) / 8 * 8; }
+__host__ __device__ constexpr int64_t carry_words(int64_t m, int64_t strips) {
+  return carry_stride16(m) / 2 * strips;
+}
 
 // ---- 16x2 SIMD helpers ---------------------------------------------------
 
@@ -141,7 +148,8 @@ __device__ __forceinline__ LaneCols lane_cols(int64_t col, int64_t n) {
   LaneCols c;
   c.shift = (uint32_t)(col & 31);
   const int64_t valid = n - col;
-  c.mask = valid <= 0 ? 0u : (valid >= P ? ((1u << P) - 1u) : ((1u << valid) - 1u));
+  const uint32_t full = P >= 32 ? 0xffffffffu : ((1u << (P & 31)) - 1u);
+  c.mask = valid <= 0 ? 0u : (valid >= P ? full : ((1u << valid) - 1u));
   return c;
 }
 
@@ -185,8 +193,12 @@ __device__ __forceinline__ uint32_t pair_mask(const Cells<P, MS_U8>& lo,
 template <int P>
 __device__ __forceinline__ uint32_t pair_mask(const Cells<P, MS_BITS32>& lo,
                                               const Cells<P, MS_BITS32>& hi, int k) {
-  const uint32_t w = (lo.bits & 0xffffu) | (hi.bits << 16);
-  return prmt(w << (15 - k), 0u, 0xBB99u);
+  // cells k of both tiles at bits k and 16 + k of one word (columns 16..31
+  // of a 32-column chunk use the upper halves), then shifted to bits 15 and
+  // 31 and replicated across their halves
+  const uint32_t w = k < 16 ? ((lo.bits & 0xffffu) | (hi.bits << 16))
+                            : ((lo.bits >> 16) | (hi.bits & 0xffff0000u));
+  return prmt(w << (15 - (k & 15)), 0u, 0xBB99u);
 }
 
 // ---- results --------------------------------------------------------------

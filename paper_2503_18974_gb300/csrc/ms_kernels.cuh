@@ -15,14 +15,14 @@
 // relies on every unflagged cell having dp <= halo.
 //
 // Lanes are skewed by one row: at step s lane l works on window row s - l,
-// so what lane l needs from lane l-1 (the row's horizontal run carry Q and
-// the diagonal A of the previous row) was produced one step earlier and is
-// passed with two shuffles; nothing waits inside a step.
+// so what lane l needs from lane l-1 (A of lane l-1's last column on this row
+// and on the row above) was produced one step earlier and is passed with two
+// shuffles; nothing waits inside a step.
 //
 // Fix-up.  If a matrix has flagged cells, their box [rlo, rhi) x [clo, chi)
 // grown by the halo up and left is recomputed exactly as one window: its
 // columns are split into strips of kFixW, one warp per strip, and each strip
-// takes the exact horizontal carry of its left neighbour row by row through
+// takes the exact A of its left neighbour's last column row by row through
 // global memory (release/acquire flags, bounded waits).  A square whose
 // corner lies in the box and which reached above the grown window would
 // contain a square of side > halo ending on the row just above rlo, and that
@@ -84,15 +84,23 @@ __device__ __forceinline__ Tile empty_tile() {
 }
 
 // ---- input staging ---------------------------------------------------------
-// Each warp owns a ring of kRing slots in shared memory; a slot holds one row
-// step of both tiles: [tile][lane][16 bytes].  Lane l copies its own column
-// chunk of window row (s - l + kRing) into the slot it consumes at step s with
-// cp.async (no registers held while the copy is in flight), so loads run
-// kRing steps ahead of use.  Edge and unaligned chunks, and chunks of fewer
-// than 4 bytes, are loaded synchronously into the same slot.
-constexpr int kRing = 8;
-constexpr int kRingSlotBytes = 2 * 32 * 16;
-constexpr int kRingWarpBytes = kRing * kRingSlotBytes;
+// Each warp owns a ring of slots in shared memory (kRingWarpBytes); a slot
+// holds one row step of both tiles: [tile][lane][kLane bytes].  Lane l copies
+// its own column chunk of window row (s - l + depth) into the slot it
+// consumes at step s with cp.async (no registers held while the copy is in
+// flight), so loads run `depth` steps ahead of use.  Edge and unaligned
+// chunks, and chunks of fewer than 4 bytes, are loaded synchronously into the
+// same slot.  32-byte chunks (uint8, P = 32) get half as many, twice as large
+// slots.
+constexpr int kRingWarpBytes = 8192;
+
+template <int P, int FMT>
+struct RingGeom {
+  static constexpr int kLane = (FMT == MS_U8 && P > 16) ? 32 : 16;  // bytes per lane and tile
+  static constexpr int kSlot = 2 * 32 * kLane;
+  static constexpr int kDepth = kRingWarpBytes / kSlot;
+  static_assert((kDepth & (kDepth - 1)) == 0 && kDepth >= 2, "ring depth: a power of two");
+};
 
 __device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int bytes_copy,
                                          int bytes_src) {
@@ -117,6 +125,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // Streams one lane's column chunk of a tile down the window into its ring.
 template <int P, int FMT>
 struct AsyncReader {
+  using G = RingGeom<P, FMT>;
   static constexpr int kBytes = FMT == MS_U8 ? P : 4;  // chunk bytes
   const uint8_t* ptr;   // chunk of window row `row`
   const uint8_t* safe;  // a valid address (zero-fill copies read nothing)
@@ -131,7 +140,7 @@ struct AsyncReader {
     const int64_t col = g.wc0 + (int64_t)P * lane;
     row = first_row;
     nrows = g.nrows;
-    dst = ring + half * 512 + lane * 16;
+    dst = ring + half * (32 * G::kLane) + lane * G::kLane;
     safe = g.base;
     if constexpr (FMT == MS_U8) {
       stride = g.ld;
@@ -147,32 +156,52 @@ struct AsyncReader {
     }
     // slots start as zeros: mode 0 never writes, the others overwrite
 #pragma unroll
-    for (int k = 0; k < kRing; ++k)
-      asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst + k * kRingSlotBytes),
-                   "r"(0u) : "memory");
+    for (int k = 0; k < G::kDepth; ++k)
+#pragma unroll
+      for (int h = 0; h < G::kLane; h += 16)
+        asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst + k * G::kSlot + h),
+                     "r"(0u) : "memory");
   }
 
   // copy window row `row` into `slot` and advance
   __device__ __forceinline__ void issue(int slot) {
     const bool ok = (unsigned)row < (unsigned)nrows;
-    const uint32_t d = dst + slot * kRingSlotBytes;
+    const uint32_t d = dst + slot * G::kSlot;
     if (mode == 1) {
-      cp_async(d, ok ? (const void*)ptr : (const void*)safe, kBytes, ok ? kBytes : 0);
+      const uint8_t* src = ok ? ptr : safe;
+      if constexpr (kBytes > 16) {
+        cp_async(d, src, 16, ok ? 16 : 0);
+        cp_async(d + 16, src + 16, 16, ok ? 16 : 0);
+      } else {
+        cp_async(d, src, kBytes, ok ? kBytes : 0);
+      }
     } else if (mode == 2) {
-      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      constexpr int NW = G::kLane / 4;
+      uint32_t w[NW];
+#pragma unroll
+      for (int b = 0; b < NW; ++b) w[b] = 0u;
       if (ok)
         for (int b = 0; b < nvalid; ++b) w[b >> 2] |= (uint32_t)__ldg(ptr + b) << (8 * (b & 3));
-      asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(d), "r"(w[0]), "r"(w[1]),
-                   "r"(w[2]), "r"(w[3]) : "memory");
+#pragma unroll
+      for (int h = 0; h < NW; h += 4)
+        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(d + 4 * h), "r"(w[h]),
+                     "r"(w[h + 1]), "r"(w[h + 2]), "r"(w[h + 3]) : "memory");
     }
     ptr += stride;
     ++row;
   }
 
   __device__ __forceinline__ void read(int slot, Raw<P, FMT>& r) const {
-    const uint32_t a = dst + slot * kRingSlotBytes;
+    const uint32_t a = dst + slot * G::kSlot;
     if constexpr (FMT == MS_U8) {
-      if constexpr (Raw<P, MS_U8>::W == 4) {
+      if constexpr (Raw<P, MS_U8>::W == 8) {
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3])
+                     : "r"(a) : "memory");
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r.w[4]), "=r"(r.w[5]), "=r"(r.w[6]), "=r"(r.w[7])
+                     : "r"(a + 16) : "memory");
+      } else if constexpr (Raw<P, MS_U8>::W == 4) {
         asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                      : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3])
                      : "r"(a) : "memory");
@@ -194,11 +223,12 @@ __device__ __forceinline__ uint32_t warp_ring() {
   return (uint32_t)__cvta_generic_to_shared(ms_dyn_smem) + (threadIdx.x >> 5) * kRingWarpBytes;
 }
 
-// Left-edge carries of a strip in the fix-up (mode 1).
+// Left-edge carries of a strip in the fix-up (mode 1): A of the left
+// strip's last column per window row (16 bits), published 8 rows at a time.
 struct StripIO {
-  const uint32_t* carry_in;   // null for the first strip (zero boundary)
+  const uint16_t* carry_in;   // null for the first strip (zero boundary); 16-B aligned
   const int32_t* progress_in;
-  uint32_t* carry_out;        // null for the last strip
+  uint16_t* carry_out;        // null for the last strip
   int32_t* progress_out;
   int32_t* status;
   int32_t hold;               // test hook: never publish (the neighbour's wait must time out)
@@ -238,20 +268,16 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
                                           uint32_t ring) {
   const int lane = threadIdx.x & 31;
   constexpr uint32_t kB2 = kBias * 0x10001u;
-  constexpr uint32_t kClamp2 = (kBias - 1) * 0x10001u;
-  constexpr int D = kRing;  // rows of input in flight per lane
-  static_assert((D & (D - 1)) == 0, "the ring size must be a power of two");
+  constexpr int D = RingGeom<P, FMT>::kDepth;  // rows of input in flight per lane
   const int nmax = max(ta.nrows, tb.nrows);
   const int nsteps = nmax + 31;
 
-  uint32_t Z[P], Ap[P];
+  uint32_t Ap[P];  // A of the lane's columns on the last row computed
 #pragma unroll
-  for (int k = 0; k < P; ++k) {
-    Z[k] = kB2;
-    Ap[k] = kB2;
-  }
-  uint32_t pubQ = 0, pubA = kB2;
+  for (int k = 0; k < P; ++k) Ap[k] = kB2;
+  uint32_t pubL = kB2, pubD = kB2;  // A of the lane's last column: this row, the row above
   uint32_t carryA_prev = kBias;  // fix-up: A of the left strip's last column, previous row
+  uint4 cq = make_uint4(0u, 0u, 0u, 0u);  // fix-up: the next carries, 16 bits per row
   bool gave_up = false;
   ba.val = bb.val = 0;
   ba.row = ba.col = bb.row = bb.col = -1;
@@ -291,8 +317,10 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
     {
       const int d = s & (D - 1);
       const int ir = s - lane;
-      uint32_t qn = __shfl_up_sync(kFull, pubQ, 1);
-      uint32_t an = __shfl_up_sync(kFull, pubA, 1);
+      // A of the left neighbour's last column on this row and the row above
+      // (lane l-1 produced both one step earlier, on the same window row)
+      uint32_t al = __shfl_up_sync(kFull, pubL, 1);
+      uint32_t ad = __shfl_up_sync(kFull, pubD, 1);
       cp_async_wait<D - 1>();
       Raw<P, FMT> rlo, rhi;
       rda.read(d, rlo);
@@ -303,54 +331,67 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
         const uint32_t I = (uint32_t)ir + 1u + kBias;
         const uint32_t I2 = I * 0x10001u;
         if (lane == 0) {
-          // left window edge: a zero column (Q = I, A = I - 1 for dp = 0)
-          qn = I2;
-          an = I2 - 0x10001u;
+          // left window edge: a zero column (dp = 0, so A = I on this row and
+          // I - 1 on the row above)
+          al = I2;
+          ad = I2 - 0x10001u;
           if constexpr (MODE == 1) {
             if (io.carry_in) {
-              if (!gave_up) {
-                int spins = 0;
-                const unsigned long long t0 = global_ns();
-                while (ld_acquire(io.progress_in) <= ir) {
-                  if (++spins > kSpinLimit || global_ns() - t0 > kWaitLimitNs) {
-                    gave_up = true;
-                    atomicExch(io.status, (int)MS_ERR_TIMEOUT);
-                    break;
+              if ((ir & 7) == 0) {
+                // the next 8 rows of carries: wait until the left strip has
+                // published them (bounded), then one 16-byte load from L2
+                const int need = min(ir + 8, ta.nrows);
+                if (!gave_up) {
+                  int spins = 0;
+                  const unsigned long long t0 = global_ns();
+                  while (ld_acquire(io.progress_in) < need) {
+                    if (++spins > kSpinLimit || global_ns() - t0 > kWaitLimitNs) {
+                      gave_up = true;
+                      atomicExch(io.status, (int)MS_ERR_TIMEOUT);
+                      break;
+                    }
+                    __nanosleep(64);
                   }
-                  __nanosleep(100);
                 }
+                cq = __ldcg(reinterpret_cast<const uint4*>(io.carry_in + ir));
               }
-              const uint32_t c = io.carry_in[ir];
-              qn = (qn & 0xffff0000u) | (c & 0xffffu);
-              an = (an & 0xffff0000u) | carryA_prev;
-              carryA_prev = c >> 16;
+              const uint32_t c = cq.x & 0xffffu;
+              cq.x = __funnelshift_r(cq.x, cq.y, 16);
+              cq.y = __funnelshift_r(cq.y, cq.z, 16);
+              cq.z = __funnelshift_r(cq.z, cq.w, 16);
+              cq.w >>= 16;
+              al = (al & 0xffff0000u) | c;
+              ad = (ad & 0xffff0000u) | carryA_prev;
+              carryA_prev = c;
             }
           }
         }
-        // Q >= kBias - 1 keeps every half >= 1 through the chain below, so the
-        // packed decrement by 0x00010001 never borrows across halves.
-        uint32_t Q = vmax2(qn, kClamp2), Ad = an, rmin = 0xffffffffu;
+        // dp = 1 + min(up, left, diagonal) on a one, 0 on a zero; in row
+        // units A = I - dp this is A = max(A_up, A_diag, A_left - 1) on a one
+        // and I on a zero.  Every A is at least kBias, so the packed
+        // decrement by 0x00010001 never borrows across halves.  (Selecting I
+        // before the last max would shorten the chain along the row to two
+        // operations, but measured slower.)
+        uint32_t rmin = 0xffffffffu;
 #pragma unroll
         for (int k = 0; k < P; ++k) {
           const uint32_t msk = pair_mask<P>(clo, chi, k);
-          const uint32_t zk = select_bits(Z[k], I2, msk);
-          Z[k] = zk;
-          Q = select_bits(Q - 0x00010001u, I2, msk);
-          const uint32_t an_k = vmax2(vmax2(Ad, zk), Q);
-          Ad = Ap[k];
-          Ap[k] = an_k;
-          rmin = vmin2(rmin, an_k);
+          const uint32_t up = Ap[k];
+          const uint32_t t = vmax2(vmax2(up, ad), al - 0x00010001u);
+          ad = up;
+          al = select_bits(t, I2, msk);
+          Ap[k] = al;
+          rmin = vmin2(rmin, al);
         }
-        pubQ = Q;
-        pubA = Ad;  // A of this lane's last column, previous row
+        pubL = al;
+        pubD = ad;  // A of this lane's last column, row above
 
         if constexpr (MODE == 1) {
           if (lane == 31 && io.carry_out) {
-            io.carry_out[ir] = (Q & 0xffffu) | (Ap[P - 1] << 16);
-            if ((((ir + 1) & 7) == 0 || ir + 1 == ta.nrows) && !io.hold) {
-              __threadfence();
+            io.carry_out[ir] = (uint16_t)al;
+            // the release orders this lane's carry stores before the count
+            if ((((ir + 1) & 7) == 0 || ir + 1 == ta.nrows) && !io.hold)
               st_release(io.progress_out, ir + 1);
-            }
           }
         }
 
@@ -507,7 +548,8 @@ __device__ __forceinline__ void batch_task(const Job* jobs, const PairTask& t) {
 }
 
 // Warps take tasks (tile pairs of one format and lane width, longest first)
-// from an atomic queue until it runs dry.
+// from an atomic queue until it runs dry.  Batched matrices use at most 16
+// columns per lane, which keeps this kernel within 128 registers.
 static __global__ void __launch_bounds__(256, 2) k_batch_tiles(const Job* __restrict__ jobs,
                                                         const PairTask* __restrict__ tasks,
                                                         int ntasks, int* queue) {
@@ -519,27 +561,26 @@ static __global__ void __launch_bounds__(256, 2) k_batch_tiles(const Job* __rest
     if (t >= ntasks) break;
     const PairTask task = tasks[t];
     const Job& A = jobs[task.job_a];
-    const int key = A.fmt * 32 + A.P;
+    const int key = A.fmt * 64 + A.P;
     switch (key) {
-      case MS_U8 * 32 + 1: batch_task<1, MS_U8>(jobs, task); break;
-      case MS_U8 * 32 + 2: batch_task<2, MS_U8>(jobs, task); break;
-      case MS_U8 * 32 + 4: batch_task<4, MS_U8>(jobs, task); break;
-      case MS_U8 * 32 + 8: batch_task<8, MS_U8>(jobs, task); break;
-      case MS_U8 * 32 + 16: batch_task<16, MS_U8>(jobs, task); break;
-      case MS_BITS32 * 32 + 1: batch_task<1, MS_BITS32>(jobs, task); break;
-      case MS_BITS32 * 32 + 2: batch_task<2, MS_BITS32>(jobs, task); break;
-      case MS_BITS32 * 32 + 4: batch_task<4, MS_BITS32>(jobs, task); break;
-      case MS_BITS32 * 32 + 8: batch_task<8, MS_BITS32>(jobs, task); break;
+      case MS_U8 * 64 + 1: batch_task<1, MS_U8>(jobs, task); break;
+      case MS_U8 * 64 + 2: batch_task<2, MS_U8>(jobs, task); break;
+      case MS_U8 * 64 + 4: batch_task<4, MS_U8>(jobs, task); break;
+      case MS_U8 * 64 + 8: batch_task<8, MS_U8>(jobs, task); break;
+      case MS_U8 * 64 + 16: batch_task<16, MS_U8>(jobs, task); break;
+      case MS_BITS32 * 64 + 1: batch_task<1, MS_BITS32>(jobs, task); break;
+      case MS_BITS32 * 64 + 2: batch_task<2, MS_BITS32>(jobs, task); break;
+      case MS_BITS32 * 64 + 4: batch_task<4, MS_BITS32>(jobs, task); break;
+      case MS_BITS32 * 64 + 8: batch_task<8, MS_BITS32>(jobs, task); break;
       default: batch_task<16, MS_BITS32>(jobs, task); break;
     }
   }
 }
 
-// Size-only tiles fit 128 registers (two 256-thread blocks per SM); the dp-map
-// variant keeps more values live and runs one block per SM.
-// Single matrix: the job travels as a kernel parameter.
+// Every variant fits 128 registers without spills, so two 256-thread blocks
+// share an SM.  Single matrix: the job travels as a kernel parameter.
 template <int P, int FMT, bool DPMAP>
-__global__ void __launch_bounds__(256, DPMAP ? 1 : 2) k_tiles_one(const Job job, int64_t ntiles) {
+__global__ void __launch_bounds__(256, 2) k_tiles_one(const Job job, int64_t ntiles) {
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   tile_pass_warp<P, FMT, DPMAP>(&job, 1, ntiles, w);
 }
@@ -902,9 +943,11 @@ __device__ __forceinline__ void fixup_job(const Job& j) {
       g.c0 = clo;
       g.aligned = j.aligned;
       StripIO io;
-      io.carry_in = s > 0 ? j.carry + (int64_t)(s - 1) * j.m : nullptr;
+      uint16_t* carry16 = reinterpret_cast<uint16_t*>(j.carry);
+      const int64_t cs = carry_stride16(j.m);
+      io.carry_in = s > 0 ? carry16 + (int64_t)(s - 1) * cs : nullptr;
       io.progress_in = s > 0 ? j.progress + (s - 1) : nullptr;
-      io.carry_out = (s + 1 < nstrips) ? j.carry + (int64_t)s * j.m : nullptr;
+      io.carry_out = (s + 1 < nstrips) ? carry16 + (int64_t)s * cs : nullptr;
       io.progress_out = j.progress + s;
       io.status = &st->status;
       io.hold = (s == 0) ? j.test_hold : 0;

@@ -12,7 +12,7 @@
 // Where its scratch lives: the per-matrix result state, the fix-up progress
 // flags and the fix-up strip carries sit in one file-scope device array,
 // g_noalloc_scratch, sized for matrices of up to kNoAllocMaxRows x
-// kNoAllocMaxCols cells (see the sizes below, about 1.1 MiB).  Every GPU that
+// kNoAllocMaxCols cells (see the sizes below, about 0.53 MiB).  Every GPU that
 // loads this library holds that array until the process exits.  The caller
 // still passes the input matrix and the result buffer.
 //
@@ -37,7 +37,8 @@ constexpr int kNoAllocMaxStrips =
     (int)((kNoAllocMaxCols + ms::kHalo + ms::kFixW - 1) / ms::kFixW + 1);
 constexpr size_t kStateBytes = 256;
 constexpr size_t kProgressBytes = ((kNoAllocMaxStrips * sizeof(int32_t) + 255) / 256) * 256;
-constexpr size_t kCarryBytes = (size_t)kNoAllocMaxRows * kNoAllocMaxStrips * sizeof(uint32_t);
+constexpr size_t kCarryBytes =
+    (size_t)ms::carry_words(kNoAllocMaxRows, kNoAllocMaxStrips) * sizeof(uint32_t);
 constexpr size_t kScratchBytes = kStateBytes + kProgressBytes + kCarryBytes;
 constexpr int kMaxDevices = 64;
 constexpr int kThreads = 256;

@@ -91,6 +91,38 @@ def test_many_bands_and_planted_squares_cross_tiles(ctx, band_rows):
         ctx.set_tuning(band_rows=0)
 
 
+@pytest.mark.parametrize("lane_cols", [1, 2, 4, 8, 16, 32])
+def test_every_lane_width(ctx, lane_cols):
+    """Each tile width forced on ragged shapes (edge chunks, several strips,
+    several bands), with planted squares above the halo crossing strip and
+    band edges: every entry point and both formats against the oracle."""
+    ctx.set_tuning(band_rows=64, lane_cols=lane_cols)
+    try:
+        rng = np.random.default_rng(500 + lane_cols)
+        W = 32 * lane_cols
+        for t, (m, n) in enumerate([(150, 3 * W - 40 + 7), (97, W + 1), (300, 2 * W + 33),
+                                    (70, max(W - 5, 1))]):
+            a = gen.bernoulli_u8(m, n, 0.85, seed=7000 + 10 * lane_cols + t)
+            s = min(m, n, 70)
+            if s > 33:
+                r0 = int(rng.integers(0, m - s + 1))
+                c0 = min(max(W - s // 2, 0), n - s)
+                a[r0:r0 + s, c0:c0 + s] = 1
+            run_all_paths(ctx, a, check_map=(m * n <= 400_000), pads=(1,))
+    finally:
+        ctx.set_tuning()
+
+
+def test_wide_matrix_automatic_lane_width(ctx):
+    """Wide size-only inputs take 32 columns per lane by default; the dp map
+    keeps 16.  Both must agree with the oracle across many strips."""
+    m, n = 400, 6000
+    a = gen.bernoulli_u8(m, n, 0.9, seed=8123)
+    a[100:190, 2000:2090] = 1
+    a[300:340, 5950:5990] = 1
+    run_all_paths(ctx, a, check_map=True, pads=(0, 1))
+
+
 def test_squares_on_tile_edges(ctx):
     ctx.set_tuning(band_rows=64)
     try:
