@@ -480,6 +480,18 @@ def run_ours(args, world, rank, local, pg):
     batch_headline = args.workload == "c4"
     multi = len(wl.mats) > 1 and not wl.dpmap
 
+    # the plain form: one autotune per workload class (format, log2 cells) on
+    # a representative matrix, cached in the context for the plain calls
+    plain_tuned = {}
+    if not wl.dpmap and not args.band_rows and not args.lane_cols and packed_path == 0:
+        classes = {}
+        for mt in wl.mats:
+            classes.setdefault((mt.fmt, int(math.log2(max(mt.m * mt.n, 1)))), []).append(mt)
+        for key, group in sorted(classes.items()):
+            rep = sorted(group, key=lambda mt: mt.m * mt.n)[len(group) // 2]
+            plain_tuned[f"fmt{key[0]}_2^{key[1]}"] = ctx.autotune(
+                [rep.args()[:2] if rep.fmt else rep.args()[0]])
+
     # the batched form: autotuned, then captured in a CUDA graph
     graph = None
     tuned = None
@@ -573,6 +585,8 @@ def run_ours(args, world, rank, local, pg):
             "how": ("one ms_max_square call per matrix, eager launches" if batch_headline else
                     "one ms_batch per step (autotuned, persistent tile queue), graph replay")},
             "autotuned": tuned}
+    if plain_tuned:
+        compare = dict(compare or {}, plain_autotuned=plain_tuned)
 
     # e2e: pinned host inputs copied to fixed device buffers, the public call
     # (ms_max_square per matrix, or ms_batch), results read back, per step

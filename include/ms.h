@@ -208,7 +208,8 @@ ms_status ms_get_tuning(ms_ctx* ctx, ms_tuning* t);
 /* Autotuner (a library feature; the paper has no counterpart).  Times the
  * work of ms_max_square (count == 1) or ms_batch (count > 1) on the given
  * matrices for each candidate tuning -- band heights 32..1024 and the
- * automatic choice, lane widths 16, 32 and the automatic choice, and for
+ * automatic choice, lane widths 2..32 and the automatic choice (single
+ * matrices only), and for
  * MS_BITS32 size-only work both packed paths --
  * keeps the fastest, and caches it in the context under the workload's class
  * (entry point, format mix, log2 of the cell count, log2 of the matrix

@@ -140,22 +140,6 @@ bool capturing(cudaStream_t s) {
   return cs != cudaStreamCaptureStatusNone;
 }
 
-// Columns per lane.  Very large size-only matrices take 32 (fewer
-// instructions and halo columns per cell, and still enough tiles to fill the
-// GPU); narrow ones take the narrowest tile covering them; the rest, and the
-// dp map (its stores keep more values live), take 16.  A 32-column tile has
-// no room for a second strip, so lane width 1 only serves n <= 32.
-int choose_P(int64_t m, int64_t n, bool dp, int32_t forced) {
-  if (forced > 1 || (forced == 1 && n <= 32)) return forced;
-  if (forced == 1) return 2;
-  if (n <= 32) return 1;
-  if (n <= 64) return 2;
-  if (n <= 128) return 4;
-  if (n <= 256) return 8;
-  if (dp || m * n < ((int64_t)1 << 29)) return 16;
-  return 32;
-}
-
 int64_t strips_for(int64_t n, int P) {
   const int64_t W = 32 * P;
   if (n <= W) return 1;
@@ -179,6 +163,53 @@ int64_t auto_band_rows_for(int64_t work_rows /* sum of m * strips */) {
 
 int auto_band_rows(int64_t m, int64_t strips) {
   return (int)std::min<int64_t>(auto_band_rows_for(m * strips), std::max<int64_t>(m, 1));
+}
+
+// Estimated cycles of one matrix's tile pass with P columns per lane: the
+// steps of a tile (band + 32 halo rows + 31 lane-skew steps) times the cycles
+// of one step, which is one warp's latency (about 3 cycles per instruction)
+// while few warps share a scheduler and the issue time of all of them when
+// many do.  Instructions per warp step: a fixed part (input staging, carries,
+// bookkeeping) plus the cells; constants from profiles of this kernel.
+double tile_cost(int64_t m, int64_t n, int P, int sms) {
+  const int64_t strips = strips_for(n, P);
+  const int64_t br = auto_band_rows(m, strips);
+  const int64_t bands = (m + br - 1) / br;
+  const double warps = (double)((bands * strips + 1) / 2);
+  const double waves = std::ceil(warps / (16.0 * sms));  // two 8-warp blocks per SM
+  const double per_sched = std::min(4.0, warps / waves / (4.0 * sms));
+  const double ipstep = 90.0 + 8.5 * P;
+  const double cyc = std::max(3.0 * ipstep, per_sched * ipstep / 0.9);
+  return waves * (double)(br + 63) * cyc;
+}
+
+// Columns per lane.  Narrow matrices take the narrowest tile covering them;
+// the others, alone, the width with the lowest estimated cost (small ones are
+// latency-bound and want short steps and many tiles, very large ones want
+// few instructions and halo columns per cell).  The dp map stays at 16 or
+// below (its stores keep more values live).  A 32-column tile has no room
+// for a second strip, so lane width 1 only serves n <= 32.
+int choose_P(int64_t m, int64_t n, bool dp, int32_t forced, int max_P, int sms) {
+  // sms == 0: a batch, where many matrices share one launch and the widest
+  // tile (fewest instructions per cell) is best
+  if (forced > 1 || (forced == 1 && n <= 32)) return std::min(forced, max_P);
+  if (forced == 1) return 2;
+  if (n <= 32) return 1;
+  if (n <= 64) return 2;
+  if (n <= 128) return 4;
+  if (n <= 256) return 8;
+  const int top = std::min(dp ? 16 : 32, max_P);
+  if (sms == 0) return std::min(16, top);
+  int best = std::min(16, top);
+  double best_cost = tile_cost(m, n, best, sms);
+  for (int P = 2; P <= top; P *= 2) {
+    const double c = tile_cost(m, n, P, sms);
+    if (c < best_cost * 0.97) {  // prefer the default width on near ties
+      best = P;
+      best_cost = c;
+    }
+  }
+  return best;
 }
 
 // Workload class for the autotune cache: entry point (single / batch),
@@ -223,7 +254,7 @@ ms_status check_matrix(const ms_matrix* in) {
   return MS_OK;
 }
 
-Job plan_job(const ms_tuning& tune, const ms_matrix* in, bool dp, int max_P = 32) {
+Job plan_job(const ms_tuning& tune, const ms_matrix* in, bool dp, int max_P, int sms) {
   Job j;
   std::memset(&j, 0, sizeof(j));
   j.data = in->data;
@@ -231,7 +262,7 @@ Job plan_job(const ms_tuning& tune, const ms_matrix* in, bool dp, int max_P = 32
   j.n = in->n;
   j.ld = in->ld;
   j.fmt = in->fmt;
-  j.P = std::min(choose_P(in->m, in->n, dp, tune.lane_cols), max_P);
+  j.P = choose_P(in->m, in->n, dp, tune.lane_cols, max_P, sms);
   if (in->m > 0 && in->n > 0) {
     j.strips = (int32_t)strips_for(in->n, j.P);
     j.band_rows = tune.band_rows > 0 ? (int32_t)std::min<int64_t>(tune.band_rows, in->m)
@@ -495,7 +526,7 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   DeviceGuard g(ctx->device);
   const ms_tuning tune = effective_tuning(ctx, in, 1, false);
   if (!dp && bits_search_applies(tune, in)) return run_bits_search(ctx, in, out_dev, s);
-  Job j = plan_job(tune, in, dp != nullptr);
+  Job j = plan_job(tune, in, dp != nullptr, 32, ctx->sms);
   st = ensure_workspace(ctx, 1, ms::carry_words(j.m, j.strips_fix), j.strips_fix, s);
   if (st != MS_OK) return st;
   const int64_t bw = dp ? 0 : bitfix_words(j);
@@ -505,7 +536,9 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   j.tile0 = 0;
   j.dp = dp;
   j.ld_dp = ld_dp;
-  j.dp_aligned = dp && (reinterpret_cast<uintptr_t>(dp) % 16 == 0) && (ld_dp % 4 == 0);
+  const uintptr_t dpa = reinterpret_cast<uintptr_t>(dp);
+  j.dp_aligned = !dp ? 0 : (dpa % 32 == 0 && ld_dp % 8 == 0) ? 2
+                           : (dpa % 16 == 0 && ld_dp % 4 == 0) ? 1 : 0;
   j.out = out_dev;
   j.st = ctx->d_states;
   j.carry = ctx->d_carry;
@@ -658,7 +691,7 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   std::vector<Job> jobs((size_t)count);
   int64_t carry = 0, progress = 0, work = 0;
   for (int32_t i = 0; i < count; ++i) {
-    jobs[i] = plan_job(tune, &ins_host[i], false, 16);  // the batch kernel: P <= 16
+    jobs[i] = plan_job(tune, &ins_host[i], false, 16, 0);  // the batch kernel: P <= 16
     carry += ms::carry_words(jobs[i].m, jobs[i].strips_fix);
     progress += jobs[i].strips_fix;
     work += jobs[i].m * (int64_t)jobs[i].strips;
@@ -816,7 +849,7 @@ ms_status ms_autotune(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_
   const bool packed_single = !batch && ins_host[0].fmt == MS_BITS32;
   std::vector<ms_tuning> cands;
   const int rows[] = {0, 32, 64, 128, 256, 512, 1024};
-  const int lanes[] = {0, 16, 32};
+  const int lanes[] = {0, 2, 4, 8, 16, 32};
   for (int pp = 0; pp <= (packed_single ? 1 : 0); ++pp)
     for (int lc : lanes)
       for (int r : rows) {

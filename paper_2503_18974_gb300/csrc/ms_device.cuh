@@ -49,7 +49,7 @@ struct Job {
   int64_t tile0;           // index of this job's first tile in its launch group
   int32_t* dp;             // optional dp map (device), may be null
   int64_t ld_dp;
-  int32_t dp_aligned;      // dp and ld_dp allow 16-byte vector stores
+  int32_t dp_aligned;      // dp and ld_dp allow 32-byte (2) or 16-byte (1) vector stores
   int32_t pad;
   ms_result* out;
   JobState* st;

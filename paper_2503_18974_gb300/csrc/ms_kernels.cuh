@@ -241,7 +241,15 @@ __device__ __forceinline__ void store_dp(int32_t* p, const uint32_t* Ap, uint32_
   auto val = [&](int k) -> int {
     return (int)I - (int)(HI ? (Ap[k] >> 16) : (Ap[k] & 0xffffu));
   };
-  if (aligned && col + P <= n && (P % 4) == 0) {
+  if (aligned == 2 && col + P <= n && (P % 8) == 0) {
+    // whole 32-byte sectors per lane: no sector is shared between stores
+#pragma unroll
+    for (int k = 0; k < P; k += 8)
+      asm volatile("st.global.cs.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p + k),
+                   "r"(val(k)), "r"(val(k + 1)), "r"(val(k + 2)), "r"(val(k + 3)),
+                   "r"(val(k + 4)), "r"(val(k + 5)), "r"(val(k + 6)), "r"(val(k + 7))
+                   : "memory");
+  } else if (aligned && col + P <= n && (P % 4) == 0) {
 #pragma unroll
     for (int k = 0; k < P; k += 4) {
       int4 v;

@@ -217,6 +217,26 @@ def test_nonzero_bytes_and_strides(ctx):
     assert ctx.max_square(w, n=900).cpu().tolist() == [K, r, c, 0]
 
 
+def test_dp_map_store_alignments(ctx):
+    """The dp map through each store path: 32-byte rows (256-bit stores),
+    16-byte rows (128-bit stores) and unaligned rows (scalar stores), with
+    cells outside the map left untouched."""
+    a = gen.bernoulli_u8(200, 1500, 0.9, seed=77)
+    a[20:110, 600:690] = 1
+    (K, r, c), dref = oracle.dp(a)
+    x = to_dev(a)
+    for off, ld in [(0, 1504), (4, 1504), (1, 1503), (8, 1512)]:
+        buf = torch.full((200 * ld + 64,), -3, dtype=torch.int32, device=DEV)
+        view = buf[off:off + 200 * ld].view(200, ld)[:, :1500]
+        dp, res = ctx.dp_map(x, dp=view)
+        assert res.cpu().tolist() == [K, r, c, 0], (off, ld)
+        assert np.array_equal(view.cpu().numpy(), dref), (off, ld)
+        rest = buf.cpu().numpy().copy()
+        idx = off + np.arange(200)[:, None] * ld + np.arange(1500)[None, :]
+        rest[idx.ravel()] = -3
+        assert (rest == -3).all(), (off, ld)
+
+
 def test_generated_c1_with_dp_map(ctx):
     """256 x 256, Bernoulli(0.5), seed 0: side, witness and the full dp map."""
     a = gen.bernoulli_u8(256, 256, 0.5, seed=0)
