@@ -184,6 +184,7 @@ double ms_server_now(void);
 
 /* ---- tuning -------------------------------------------------------------
  * Launch parameters: `band_rows` = rows of a matrix that one tile counts
+ * (at most 16384)
  * (each tile also re-reads a halo of 32 rows above and 32 columns to its
  * left), `packed_path` selects, for MS_BITS32 size-only work, the bitplane
  * erosion search (1) or the byte-style tile kernel on unpacked bits (0).

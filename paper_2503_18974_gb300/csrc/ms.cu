@@ -391,6 +391,16 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
         return cudaGetLastError();
       ms::k_fixup_bits_one<FMT><<<1, 1024, sm, s>>>(j, (int64_t)(sm / 4));
     } else {
+      if (DPMAP && j.bits_scratch && !j.test_hold) {
+        // dp map: bitplane levels in the box, then every box cell's dp from
+        // them; the strip kernel below only finalises unless the levels did
+        // not fit the scratch (or the strip test hook is on)
+        const size_t smb = kBitsFixSmemBytes;
+        if (allow_smem((const void*)ms::k_fixup_dp_levels<FMT>, smb) != cudaSuccess)
+          return cudaGetLastError();
+        ms::k_fixup_dp_levels<FMT><<<1, 1024, smb, s>>>(j, (int64_t)(smb / 4));
+        ms::k_fixup_dp_cells<<<4 * ctx->sms, 256, 0, s>>>(j);
+      }
       const size_t sm = ring_bytes(ms::kFixWarps * 32);
       if (allow_smem((const void*)ms::k_fixup_one<FMT, DPMAP>, sm) != cudaSuccess)
         return cudaGetLastError();
@@ -529,7 +539,7 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   Job j = plan_job(tune, in, dp != nullptr, 32, ctx->sms);
   st = ensure_workspace(ctx, 1, ms::carry_words(j.m, j.strips_fix), j.strips_fix, s);
   if (st != MS_OK) return st;
-  const int64_t bw = dp ? 0 : bitfix_words(j);
+  const int64_t bw = bitfix_words(j);
   if (bw > 0 && bw <= kBitfixCapWords &&
       grow(ctx, ctx->d_bitfix, ctx->bitfix_cap, bw, capturing(s)) == MS_OK)
     j.bits_scratch = ctx->d_bitfix;
@@ -645,7 +655,7 @@ ms_status ms_destroy(ms_ctx* ctx) {
 
 ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t) {
   if (!ctx || !t) return MS_ERR_INVALID;
-  if (t->band_rows < 0 || t->band_rows > 65000) return MS_ERR_INVALID;
+  if (t->band_rows < 0 || t->band_rows > 16384) return MS_ERR_INVALID;
   if (t->packed_path < 0 || t->packed_path > 1) return MS_ERR_INVALID;
   if (t->test_hold_carries < 0 || t->test_hold_carries > 1) return MS_ERR_INVALID;
   if (t->lane_cols != 0 && t->lane_cols != 1 && t->lane_cols != 2 && t->lane_cols != 4 &&

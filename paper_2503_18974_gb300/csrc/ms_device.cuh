@@ -7,8 +7,8 @@
 //
 // Restatement used on the GPU.  Eq. 1 on a one cell is
 //   dp[i][j] = 1 + min(dp[i-1][j], dp[i][j-1], dp[i-1][j-1]),
-// and 0 on a zero cell.  In row units A = i + 1 - dp (one past the last row
-// the square does not cover) the minimum becomes a maximum:
+// and 0 on a zero cell.  In row units A = i + 1 - dp (the top row of the
+// largest square ending at the cell) the minimum becomes a maximum:
 //   A[i][j] = max(A[i-1][j], A[i-1][j-1], A[i][j-1] - 1)  on a one,
 //   A[i][j] = i + 1                                        on a zero,
 // because the row index of the neighbours above is one less.  The paper's

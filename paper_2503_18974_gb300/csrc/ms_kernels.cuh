@@ -761,52 +761,44 @@ __device__ __forceinline__ void grow_pass(const Plane& L, Plane& O, int o_r1, in
   O.aw1 = box[3];
 }
 
-// The three planes live in shared memory when they fit in `smem_words`
-// words (small boxes: every pass then runs from shared memory), else in the
-// job's global scratch.
+// Geometry of the bitplane fix-up of box [rlo, rhi) x [clo, chi): S_32 is
+// built on rows [ra, rhi) x words [wa, whi) (the box grown by 32 up and
+// left) from input rows [pa, rhi) x words [wa-1, whi).
+struct BitGeo {
+  int ra, wlo, whi, wa, R1, W1, pa, Wv, RP;
+  __device__ __forceinline__ BitGeo(int rlo, int rhi, int clo, int chi) {
+    ra = max(0, rlo - kHalo);
+    wlo = clo / 32;
+    whi = (chi + 31) / 32;
+    wa = max(0, clo - kHalo) / 32;
+    R1 = rhi - ra;
+    W1 = whi - wa;
+    pa = max(0, ra - 31);
+    Wv = W1 + 1;
+    RP = rhi - pa;
+  }
+};
+
+// S_32 of the geometry into s32buf (R1 x W1 words), through the input buffer
+// `in` and the vertical buffer `vb` (RP x Wv words each); returns its plane
+// with the active box of its set bits.
 template <int FMT>
-__device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int clo, int chi,
-                                           uint32_t* smem, int64_t smem_words) {
-  __shared__ unsigned long long s_first;
-  __shared__ int s_box[3][4];
-  PassBox pb{s_box, 0};
-  if (threadIdx.x == 0) {
-    s_box[0][0] = 0x7fffffff;
-    s_box[0][1] = -1;
-    s_box[0][2] = 0x7fffffff;
-    s_box[0][3] = -1;
-    s_first = ~0ull;
-  }
-  const int ra = max(0, rlo - kHalo);
-  const int wlo = clo / 32, whi = (chi + 31) / 32;
-  const int wa = max(0, clo - kHalo) / 32;
-  const int R1 = rhi - ra, W1 = whi - wa;
-  const int pa = max(0, ra - 31);
-  const int Wv = W1 + 1, RP = rhi - pa;
-  uint32_t *buf0, *buf1, *buf2;  // V_32 then levels / S_32 on the grown box / input then levels
-  if (smem && 2 * (int64_t)RP * Wv + (int64_t)R1 * W1 <= smem_words) {
-    buf2 = smem;
-    buf0 = smem + RP * Wv;
-    buf1 = smem + 2 * RP * Wv;
-  } else {
-    const int64_t cap = j.m * ((j.n + 31) / 32 + 2);
-    buf0 = j.bits_scratch;
-    buf1 = j.bits_scratch + cap;
-    buf2 = j.bits_scratch + 2 * cap;
-  }
+__device__ __forceinline__ Plane build_s32(const Job& j, const BitGeo& g, uint32_t* in,
+                                           uint32_t* vb, uint32_t* s32buf, PassBox& pb) {
+  const int RP = g.RP, Wv = g.Wv, R1 = g.R1, W1 = g.W1, ra = g.ra, wa = g.wa, pa = g.pa;
   // 1. input bits of rows [pa, rhi), words [wa-1, whi)
   for_cells(RP, Wv, [&](int rr, int cc) {
-    buf2[rr * Wv + cc] = input_word<FMT>(j, pa + rr, wa - 1 + cc);
+    in[rr * Wv + cc] = input_word<FMT>(j, pa + rr, wa - 1 + cc);
   });
   __syncthreads();
   // 2. vertical: V_32(i, w) = AND of the 32 rows ending at i, by doubling
   //    V_2k(i) = V_k(i) & V_k(i-k) over rows [pa, rhi) (5 passes, ping-pong
-  //    between buf2 and buf0, ending in buf0).  Rows above pa read as zeros,
+  //    between `in` and `vb`, ending in `vb`).  Rows above pa read as zeros,
   //    so V_k is exact on rows >= pa + k - 1, which covers every row >= ra
   //    (pa = ra - 31, or pa = 0 at the matrix top where the zeros are real).
   {
-    uint32_t* src = buf2;
-    uint32_t* dst = buf0;
+    uint32_t* src = in;
+    uint32_t* dst = vb;
     for (int k = 1; k < 32; k *= 2) {
       for_cells(RP, Wv, [&](int rr, int cc) {
         const int e = rr * Wv + cc;
@@ -820,35 +812,70 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
   }
   // 3. horizontal: S_32 = AND of 32 consecutive V_32 bits ending at each
   //    cell, on rows [ra, rhi) x words [wa, whi)
-  Plane s32{buf1, ra, wa, W1, 0, 0, 0, 0};
-  {
-    int rmin = 0x7fffffff, rmax = -1, wmin = 0x7fffffff, wmax = -1;
-    pb.begin();
-    for_cells(R1, W1, [&](int rr, int cc) {
-      const int vr = rr + (ra - pa);  // row of V_32 in its [pa, rhi) layout
-      const uint32_t x = buf0[vr * Wv + cc + 1], y = buf0[vr * Wv + cc];
-      unsigned long long z = ((unsigned long long)x << 32) | y;
-      z &= z << 1;
-      z &= z << 2;
-      z &= z << 4;
-      z &= z << 8;
-      z &= z << 16;
-      const uint32_t v = (uint32_t)(z >> 32);
-      buf1[rr * W1 + cc] = v;
-      if (v) {
-        rmin = min(rmin, ra + rr);
-        rmax = max(rmax, ra + rr);
-        wmin = min(wmin, wa + cc);
-        wmax = max(wmax, wa + cc);
-      }
-    });
-    int box[4];
-    pb.end(rmin, rmax, wmin, wmax, box);
-    s32.ar0 = box[0];
-    s32.ar1 = box[1];
-    s32.aw0 = box[2];
-    s32.aw1 = box[3];
+  Plane s32{s32buf, ra, wa, W1, 0, 0, 0, 0};
+  int rmin = 0x7fffffff, rmax = -1, wmin = 0x7fffffff, wmax = -1;
+  pb.begin();
+  for_cells(R1, W1, [&](int rr, int cc) {
+    const int vr = rr + (ra - pa);  // row of V_32 in its [pa, rhi) layout
+    const uint32_t x = vb[vr * Wv + cc + 1], y = vb[vr * Wv + cc];
+    unsigned long long z = ((unsigned long long)x << 32) | y;
+    z &= z << 1;
+    z &= z << 2;
+    z &= z << 4;
+    z &= z << 8;
+    z &= z << 16;
+    const uint32_t v = (uint32_t)(z >> 32);
+    s32buf[rr * W1 + cc] = v;
+    if (v) {
+      rmin = min(rmin, ra + rr);
+      rmax = max(rmax, ra + rr);
+      wmin = min(wmin, wa + cc);
+      wmax = max(wmax, wa + cc);
+    }
+  });
+  int box[4];
+  pb.end(rmin, rmax, wmin, wmax, box);
+  s32.ar0 = box[0];
+  s32.ar1 = box[1];
+  s32.aw0 = box[2];
+  s32.aw1 = box[3];
+  return s32;
+}
+
+__device__ __forceinline__ void pass_box_init(int (*s_box)[4]) {
+  if (threadIdx.x == 0) {
+    s_box[0][0] = 0x7fffffff;
+    s_box[0][1] = -1;
+    s_box[0][2] = 0x7fffffff;
+    s_box[0][3] = -1;
   }
+}
+
+// Size-only.  The three planes live in shared memory when they fit in
+// `smem_words` words (small boxes: every pass then runs from shared memory),
+// else in the job's global scratch.
+template <int FMT>
+__device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int clo, int chi,
+                                           uint32_t* smem, int64_t smem_words) {
+  __shared__ unsigned long long s_first;
+  __shared__ int s_box[3][4];
+  PassBox pb{s_box, 0};
+  pass_box_init(s_box);
+  if (threadIdx.x == 0) s_first = ~0ull;
+  const BitGeo g(rlo, rhi, clo, chi);
+  const int wlo = g.wlo, whi = g.whi;
+  uint32_t *buf0, *buf1, *buf2;  // V_32 then levels / S_32 on the grown box / input then levels
+  if (smem && 2 * (int64_t)g.RP * g.Wv + (int64_t)g.R1 * g.W1 <= smem_words) {
+    buf2 = smem;
+    buf0 = smem + g.RP * g.Wv;
+    buf1 = smem + 2 * g.RP * g.Wv;
+  } else {
+    const int64_t cap = j.m * ((j.n + 31) / 32 + 2);
+    buf0 = j.bits_scratch;
+    buf1 = j.bits_scratch + cap;
+    buf2 = j.bits_scratch + 2 * cap;
+  }
+  const Plane s32 = build_s32<FMT>(j, g, buf2, buf0, buf1, pb);
   // 4. doubling from 32 inside the box [rlo, rhi) x [wlo, whi), then binary
   //    search; level planes alternate between buf0 and buf2
   const int BW = whi - wlo;
@@ -887,6 +914,153 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
                                    (int64_t)(idx % (unsigned long long)j.n), j.n));
   }
   __syncthreads();
+}
+
+// ---- dp-map fix-up by bitplane levels -------------------------------------
+//
+// Cells with dp >= 33 lie in the flagged box, and there dp(i,j) is the
+// largest t with S_t(i,j).  Keep the levels L_k = S_{32*2^k} (doubling inside
+// the box until a level is empty).  A cell whose top level is k has dp in
+// [a, 2a) with a = 32*2^k, and for 0 <= D < a
+//   S_{a+D}(i,j) = L_k(i,j) & L_k(i-D,j) & L_k(i,j-D) & L_k(i-D,j-D),
+// so a binary search on D (each test three bit reads of one stored level)
+// gives dp = a + D exactly.  One block builds the levels in the job's scratch;
+// a grid then writes the dp of every box cell whose S_32 bit is set and folds
+// the largest into the matrix's key.  Levels that do not fit the scratch
+// leave the table empty, and the strip fix-up runs instead.
+
+constexpr int kMaxLevels = 12;  // 32 << 11 exceeds every supported side
+struct LevelRec {
+  int64_t off;  // words after the table
+  int32_t r0, w0, pitch;
+  int32_t ar0, ar1, aw0, aw1;
+  int32_t pad;
+};
+struct LevelTab {
+  int32_t n;  // levels stored; 0: none (no box, or the strip fix-up runs)
+  int32_t pad;
+  LevelRec lv[kMaxLevels];
+};
+constexpr int kTabWords = 256;
+static_assert(sizeof(LevelTab) <= kTabWords * 4, "level table too large");
+
+__device__ __forceinline__ uint32_t level_bit(const LevelRec& L, const uint32_t* base, int i,
+                                              int c) {
+  if (c < 0) return 0u;
+  const int w = c >> 5;
+  if (i < L.ar0 || i >= L.ar1 || w < L.aw0 || w >= L.aw1) return 0u;
+  return (base[L.off + (int64_t)(i - L.r0) * L.pitch + (w - L.w0)] >> (c & 31)) & 1u;
+}
+
+// Builds S_32 and the doubling levels of box [rlo, rhi) x [clo, chi).  The
+// input and vertical buffers use shared memory when they fit.
+template <int FMT>
+__device__ __forceinline__ void fixup_dp_levels(const Job& j, int rlo, int rhi, int clo, int chi,
+                                                uint32_t* smem, int64_t smem_words) {
+  __shared__ int s_box[3][4];
+  PassBox pb{s_box, 0};
+  pass_box_init(s_box);
+  LevelTab* tab = reinterpret_cast<LevelTab*>(j.bits_scratch);
+  uint32_t* base = j.bits_scratch + kTabWords;
+  const int64_t avail = 3 * j.m * ((j.n + 31) / 32 + 2) - kTabWords;
+  const BitGeo g(rlo, rhi, clo, chi);
+  const int64_t vw = (int64_t)g.RP * g.Wv;
+  uint32_t *in, *vb;
+  int64_t off = 0;
+  if (smem && 2 * vw <= smem_words) {
+    in = smem;
+    vb = smem + vw;
+  } else {
+    in = base;
+    vb = base + vw;
+    off = 2 * vw;
+  }
+  if (off + (int64_t)g.R1 * g.W1 > avail) return;  // does not fit: table stays empty
+  Plane cur = build_s32<FMT>(j, g, in, vb, base + off, pb);
+  if (threadIdx.x == 0)
+    tab->lv[0] = LevelRec{off, g.ra, g.wa, g.W1, cur.ar0, cur.ar1, cur.aw0, cur.aw1, 0};
+  off += (int64_t)g.R1 * g.W1;
+  int nl = 1, a = 32;
+  const int kmax = (int)min(j.m, j.n);
+  while (!cur.empty() && 2 * a <= kmax && nl < kMaxLevels) {
+    // S_2a lies inside S_a's active box and inside the box
+    const int r0 = max(cur.ar0, rlo), r1 = cur.ar1;
+    const int w0 = max(cur.aw0, g.wlo), w1 = cur.aw1;
+    if (r1 <= r0 || w1 <= w0) break;
+    const int64_t size = (int64_t)(r1 - r0) * (w1 - w0);
+    if (off + size > avail) return;
+    Plane nxt{base + off, r0, w0, w1 - w0, 0, 0, 0, 0};
+    grow_pass(cur, nxt, r1, w1, a, j.n, true, nullptr, pb);
+    if (nxt.empty()) break;
+    if (threadIdx.x == 0)
+      tab->lv[nl] = LevelRec{off, r0, w0, w1 - w0, nxt.ar0, nxt.ar1, nxt.aw0, nxt.aw1, 0};
+    off += size;
+    ++nl;
+    a *= 2;
+    cur = nxt;
+  }
+  if (threadIdx.x == 0) tab->n = nl;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(1024, 1) k_fixup_dp_levels(const Job job, int64_t smem_words) {
+  extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
+  __shared__ int32_t sbox[4];
+  if (threadIdx.x == 0) {
+    reinterpret_cast<LevelTab*>(job.bits_scratch)->n = 0;
+    sbox[0] = job.st->box[0];
+    sbox[1] = job.st->box[1];
+    sbox[2] = job.st->box[2];
+    sbox[3] = job.st->box[3];
+  }
+  __syncthreads();
+  if (sbox[1] > sbox[0] && sbox[3] > sbox[2])
+    fixup_dp_levels<FMT>(job, sbox[0], sbox[1], sbox[2], sbox[3],
+                         reinterpret_cast<uint32_t*>(ms_dyn_smem), smem_words);
+}
+
+// Exact dp of the box cells from the levels (grid-stride over S_32's active
+// region inside the box).
+static __global__ void __launch_bounds__(256) k_fixup_dp_cells(const Job j) {
+  __shared__ LevelRec s_lv[kMaxLevels];
+  const LevelTab* tab = reinterpret_cast<const LevelTab*>(j.bits_scratch);
+  const int nl = tab->n;
+  if (nl <= 0) return;
+  if ((int)threadIdx.x < nl) s_lv[threadIdx.x] = tab->lv[threadIdx.x];
+  __syncthreads();
+  const uint32_t* base = j.bits_scratch + kTabWords;
+  const int rlo = j.st->box[0], rhi = j.st->box[1], clo = j.st->box[2], chi = j.st->box[3];
+  const LevelRec& L0 = s_lv[0];
+  const int r0 = max(rlo, L0.ar0), r1 = min(rhi, L0.ar1);
+  const int c0 = max(clo, 32 * L0.aw0), c1 = min(chi, 32 * L0.aw1);
+  unsigned long long key = 0;
+  if (r1 > r0 && c1 > c0) {
+    const int W = c1 - c0;
+    const int64_t total = (int64_t)(r1 - r0) * W;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+      const int i = r0 + (int)(e / W), c = c0 + (int)(e % W);
+      if (!level_bit(L0, base, i, c)) continue;
+      int k = 0;
+      while (k + 1 < nl && level_bit(s_lv[k + 1], base, i, c)) ++k;
+      const LevelRec& L = s_lv[k];
+      int lo = 0, hi = 32 << k;  // S_{a+lo} holds, S_{a+hi} does not
+      while (hi - lo > 1) {
+        const int d = (lo + hi) >> 1;
+        if (level_bit(L, base, i - d, c) & level_bit(L, base, i, c - d) &
+            level_bit(L, base, i - d, c - d))
+          lo = d;
+        else
+          hi = d;
+      }
+      const int dpv = (32 << k) + lo;
+      j.dp[(int64_t)i * j.ld_dp + c] = dpv;
+      const unsigned long long kk = make_key(dpv, i, c, j.n);
+      key = kk > key ? kk : key;
+    }
+  }
+  key = warp_max_u64(key);
+  if ((threadIdx.x & 31) == 0 && key) atomicMax(&j.st->key, key);
 }
 
 // Writes the matrix's result from its key and leaves its state ready for the
@@ -930,7 +1104,10 @@ __device__ __forceinline__ void fixup_job(const Job& j) {
   }
   __syncthreads();
   const int rlo = sbox[0], rhi = sbox[1], clo = sbox[2], chi = sbox[3];
-  if (rhi > rlo && chi > clo) {
+  // a dp map already completed from bitplane levels needs no strips
+  const bool done = DPMAP && j.bits_scratch &&
+                    reinterpret_cast<const LevelTab*>(j.bits_scratch)->n > 0;
+  if (rhi > rlo && chi > clo && !done) {
     const int64_t br0 = max(0, rlo - kHalo);
     // rounded down to 32 columns: fix-up chunks must stay inside a packed
     // word and keep vector loads aligned (a wider window is still exact)
