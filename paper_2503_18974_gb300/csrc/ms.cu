@@ -31,6 +31,7 @@ struct ms_ctx {
   int64_t progress_cap = 0;
   uint32_t* d_bitfix = nullptr;  // bitplanes of the size-only fix-up
   int64_t bitfix_cap = 0;        // uint32 words
+  ms::TeamSync* d_sync1 = nullptr;  // barrier of a single matrix's fix-up team
 
   // batch job table: device copy, the host image it was uploaded from, and a
   // pinned staging buffer guarded by an event
@@ -278,6 +279,15 @@ Job plan_job(const ms_tuning& tune, const ms_matrix* in, bool dp, int max_P, int
 
 int64_t tiles_of(const Job& j) { return (int64_t)j.bands * j.strips; }
 
+// Blocks sharing one matrix's bitplane fix-up: the box is unknown before the
+// tile pass, so size the team by the matrix (a block per 2^23 cells for a
+// single call, per 2^18 cells in a batch, where blocks are smaller and many
+// matrices share the GPU), at most `cap`.
+int fix_team_size(int64_t cells, int cap, int shift = 23) {
+  const int64_t t = (cells + ((int64_t)1 << shift) - 1) >> shift;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(t, cap));
+}
+
 // Words of bitplane scratch the size-only fix-up of a matrix may need (three
 // planes over at most the whole matrix), and the pool cap beyond which
 // matrices fall back to the strip fix-up.
@@ -386,10 +396,16 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
     if (!DPMAP && j.bits_scratch) {
       // size-only: bitplane growth in the flagged box, planes in shared
       // memory when the box is small enough
+      // large matrices may have large boxes: a team of blocks (one per SM)
+      // then shares every pass
       const size_t sm = kBitsFixSmemBytes;
       if (allow_smem((const void*)ms::k_fixup_bits_one<FMT>, sm) != cudaSuccess)
         return cudaGetLastError();
-      ms::k_fixup_bits_one<FMT><<<1, 1024, sm, s>>>(j, (int64_t)(sm / 4));
+      const int team = fix_team_size(j.m * j.n, std::min(16, ctx->sms));
+      if (team > 1 && cudaMemsetAsync(ctx->d_sync1, 0, sizeof(ms::TeamSync), s) != cudaSuccess)
+        return cudaGetLastError();
+      ms::k_fixup_bits_one<FMT><<<team, 1024, sm, s>>>(j, (int64_t)(sm / 4),
+                                                       team > 1 ? ctx->d_sync1 : nullptr);
     } else {
       if (DPMAP && j.bits_scratch && !j.test_hold) {
         // dp map: bitplane levels in the box, then every box cell's dp from
@@ -620,6 +636,12 @@ ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes) {
     return MS_ERR_CUDA;
   }
   ctx->sms = std::max(ctx->sms, 1);
+  if (cudaMalloc(&ctx->d_sync1, sizeof(ms::TeamSync)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaEventDestroy(ctx->stage_free);
+    delete ctx;
+    return MS_ERR_OOM;
+  }
   ms_status st = ensure_workspace(ctx, 64, 1 << 16, 1024, nullptr);
   if (st != MS_OK) {
     ms_destroy(ctx);
@@ -644,6 +666,7 @@ ms_status ms_destroy(ms_ctx* ctx) {
     release(ctx, ctx->d_bst, ctx->bst_cap);
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
+    if (ctx->d_sync1) cudaFree(ctx->d_sync1);
     for (auto& ps : ctx->prof_pool) {
       cudaEventDestroy(ps.a);
       cudaEventDestroy(ps.b);
@@ -773,13 +796,35 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   }
   const int ntasks = (int)tasks.size();
 
-  // table image: [jobs | tasks | queue counter], 16-byte aligned sections
+  // size-only fix-up blocks: a team per matrix with bitplane scratch, sized by
+  // the matrix, larger teams (then larger matrices) first so that the longest
+  // fix-ups start early
+  std::vector<ms::FixTask> fix;
+  {
+    std::vector<int32_t> order;
+    for (int32_t i = 0; i < count; ++i)
+      if (jobs[i].bits_scratch && jobs[i].m > 0 && jobs[i].n > 0) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      return jobs[a].m * jobs[a].n > jobs[b].m * jobs[b].n;
+    });
+    for (int32_t i : order) {
+      const int size = fix_team_size(jobs[i].m * jobs[i].n, 16, 18);
+      for (int r = 0; r < size; ++r) fix.push_back(ms::FixTask{i, r, size, 0});
+    }
+  }
+  const int nfix = (int)fix.size();
+
+  // table image: [jobs | tasks | fix tasks | queue counter | team barriers],
+  // 16-byte aligned sections; the last two are cleared before every launch
   const size_t jobs_bytes = ((size_t)count * sizeof(Job) + 15) / 16 * 16;
   const size_t tasks_bytes = ((size_t)ntasks * sizeof(ms::PairTask) + 15) / 16 * 16;
-  const size_t table_bytes = jobs_bytes + tasks_bytes + 16;
+  const size_t fix_bytes = (size_t)nfix * sizeof(ms::FixTask);
+  const size_t clear_bytes = 16 + (size_t)count * sizeof(ms::TeamSync);
+  const size_t table_bytes = jobs_bytes + tasks_bytes + fix_bytes + clear_bytes;
   std::vector<unsigned char> image(table_bytes, 0);
   std::memcpy(image.data(), jobs.data(), (size_t)count * sizeof(Job));
   if (ntasks) std::memcpy(image.data() + jobs_bytes, tasks.data(), (size_t)ntasks * sizeof(ms::PairTask));
+  if (nfix) std::memcpy(image.data() + jobs_bytes + tasks_bytes, fix.data(), fix_bytes);
 
   // upload only when it differs from the table already on the device
   if (ctx->uploaded != image) {
@@ -807,7 +852,12 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   }
   const Job* d_jobs = reinterpret_cast<const Job*>(ctx->d_table);
   const ms::PairTask* d_tasks = reinterpret_cast<const ms::PairTask*>(ctx->d_table + jobs_bytes);
-  int* d_queue = reinterpret_cast<int*>(ctx->d_table + jobs_bytes + tasks_bytes);
+  const ms::FixTask* d_fix =
+      reinterpret_cast<const ms::FixTask*>(ctx->d_table + jobs_bytes + tasks_bytes);
+  unsigned char* d_clear = ctx->d_table + jobs_bytes + tasks_bytes + fix_bytes;
+  int* d_queue = reinterpret_cast<int*>(d_clear);
+  ms::TeamSync* d_syncs = reinterpret_cast<ms::TeamSync*>(d_clear + 16);
+  if (cudaMemsetAsync(d_clear, 0, clear_bytes, s) != cudaSuccess) return MS_ERR_CUDA;
 
   if (ntasks > 0) {
     const size_t sm = ring_bytes(kTileThreads);
@@ -823,7 +873,6 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     }
     const int wpb = kTileThreads / 32;
     const int grid = std::max(1, std::min(ctx->batch_grid, (ntasks + wpb - 1) / wpb));
-    if (cudaMemsetAsync(d_queue, 0, sizeof(int), s) != cudaSuccess) return MS_ERR_CUDA;
     ProfScope ps(ctx, s, kProfTile);
     ms::k_batch_tiles<<<grid, kTileThreads, sm, s>>>(d_jobs, d_tasks, ntasks, d_queue);
     if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
@@ -833,8 +882,9 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     if (any_bits) {
       const size_t smb = kBitsFixSmemBytes / 2;  // two blocks per SM
       if (allow_smem((const void*)ms::k_fixup_bits_mixed, smb) != cudaSuccess) return MS_ERR_CUDA;
-      ms::k_fixup_bits_mixed<<<count, ms::kBitsMixedThreads, smb, s>>>(d_jobs, count,
-                                                                      (int64_t)(smb / 4));
+      if (nfix > 0)
+        ms::k_fixup_bits_mixed<<<nfix, ms::kBitsMixedThreads, smb, s>>>(d_jobs, d_fix, d_syncs,
+                                                                        (int64_t)(smb / 4));
     }
     if (any_strip) {
       const size_t smf = ring_bytes(ms::kFixWarps * 32);

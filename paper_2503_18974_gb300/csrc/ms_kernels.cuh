@@ -622,14 +622,62 @@ struct Plane {
   __device__ __forceinline__ bool empty() const { return ar1 <= ar0 || aw1 <= aw0; }
 };
 
-// Visits the cells (r, c) of a rows x cols grid, spread over the block's
+// A team of `size` blocks sharing one matrix's bitplane passes (size 1: a
+// lone block).  Passes spread their cells over all the team's threads and end
+// with a team barrier: __syncthreads for one block; for several, an arrival
+// counter in global memory (bounded wait: on timeout the matrix's status
+// becomes MS_ERR_TIMEOUT and the block stops waiting, so nothing hangs).
+// Pass boxes and the witness minimum of several blocks live in global memory.
+struct TeamSync {            // one per matrix, zeroed before the launch
+  unsigned int arrive;       // barrier arrivals
+  unsigned int pad;
+  int box[3][4];             // pass boxes (as PassBox slots)
+  unsigned long long first;  // witness: smallest row-major index
+};
+struct Team {
+  int size, rank;
+  TeamSync* sync;  // null when size == 1
+  int32_t* status;
+  unsigned int passed;  // barriers passed
+  bool gave_up;
+  __device__ __forceinline__ int thread() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
+  __device__ __forceinline__ int threads() const { return size * (int)blockDim.x; }
+  __device__ __forceinline__ void barrier() {
+    __syncthreads();
+    if (size > 1) {
+      if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&sync->arrive, 1u);
+        const unsigned int target = (passed + 1) * (unsigned int)size;
+        if (!gave_up) {
+          int spins = 0;
+          const unsigned long long t0 = global_ns();
+          while ((unsigned int)ld_acquire(reinterpret_cast<const int32_t*>(&sync->arrive)) <
+                 target) {
+            if (++spins > kSpinLimit || global_ns() - t0 > kWaitLimitNs) {
+              gave_up = true;
+              atomicExch(status, (int)MS_ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(32);
+          }
+        }
+        __threadfence();
+      }
+      ++passed;
+      __syncthreads();
+    }
+  }
+};
+
+// Visits the cells (r, c) of a rows x cols grid, spread over the team's
 // threads in row-major order; the row/column step is kept incrementally.
 template <class F>
-__device__ __forceinline__ void for_cells(int rows, int cols, F&& f) {
+__device__ __forceinline__ void for_cells(const Team& tm, int rows, int cols, F&& f) {
   if (rows <= 0 || cols <= 0) return;
-  const int bd = (int)blockDim.x;
+  const int bd = tm.threads(), t0 = tm.thread();
   const int dr = bd / cols, dc = bd - dr * cols;
-  int r = (int)threadIdx.x / cols, c = (int)threadIdx.x - r * cols;
+  int r = t0 / cols, c = t0 - r * cols;
 #pragma unroll 2
   for (; r < rows;) {
     f(r, c);
@@ -679,19 +727,23 @@ __device__ __forceinline__ uint32_t input_word(const Job& j, int i, int w) {
 // per warp and fold into slot k % 3 with shared-memory atomics; slot
 // (k+1) % 3 is reset during pass k (its last readers finished before the
 // barrier of pass k-1), so each pass needs a single __syncthreads.
+__device__ __forceinline__ void box_reset(int* b) {
+  b[0] = 0x7fffffff;
+  b[1] = -1;
+  b[2] = 0x7fffffff;
+  b[3] = -1;
+}
 struct PassBox {
   int (*slot)[4];  // shared [3][4]: row min, row max, word min, word max
   int k;
+  Team* tm;
   __device__ __forceinline__ void begin() const {
     if (threadIdx.x == 0) {
-      int* b = slot[(k + 1) % 3];
-      b[0] = 0x7fffffff;
-      b[1] = -1;
-      b[2] = 0x7fffffff;
-      b[3] = -1;
+      box_reset(slot[(k + 1) % 3]);
+      if (tm->size > 1 && tm->rank == 0) box_reset(tm->sync->box[(k + 1) % 3]);
     }
   }
-  // all threads; returns [r0, r1) x [w0, w1) (empty: r1 <= r0)
+  // all threads of the team; returns [r0, r1) x [w0, w1) (empty: r1 <= r0)
   __device__ __forceinline__ void end(int rmin, int rmax, int wmin, int wmax, int out[4]) {
     rmin = __reduce_min_sync(0xffffffffu, rmin);
     rmax = __reduce_max_sync(0xffffffffu, rmax);
@@ -703,6 +755,23 @@ struct PassBox {
       atomicMax(b + 1, rmax);
       atomicMin(b + 2, wmin);
       atomicMax(b + 3, wmax);
+    }
+    if (tm->size > 1) {
+      __syncthreads();
+      int* g = tm->sync->box[k % 3];
+      if (threadIdx.x == 0 && b[1] >= 0) {
+        atomicMin(g + 0, b[0]);
+        atomicMax(g + 1, b[1]);
+        atomicMin(g + 2, b[2]);
+        atomicMax(g + 3, b[3]);
+      }
+      tm->barrier();
+      if (threadIdx.x == 0) {
+        b[0] = *reinterpret_cast<volatile int*>(g + 0);
+        b[1] = *reinterpret_cast<volatile int*>(g + 1);
+        b[2] = *reinterpret_cast<volatile int*>(g + 2);
+        b[3] = *reinterpret_cast<volatile int*>(g + 3);
+      }
     }
     __syncthreads();
     out[0] = b[0];
@@ -727,7 +796,7 @@ __device__ __forceinline__ void grow_pass(const Plane& L, Plane& O, int o_r1, in
   int rmin = 0x7fffffff, rmax = -1, wmin = 0x7fffffff, wmax = -1;
   unsigned long long f = ~0ull;
   pb.begin();
-  for_cells(r1 - r0, w1 - w0, [&](int rr, int cc) {
+  for_cells(*pb.tm, r1 - r0, w1 - w0, [&](int rr, int cc) {
     const int i = r0 + rr, w = w0 + cc;
     const uint32_t a0 = L.get(i, w), a1 = L.get(i - d, w);
     uint32_t a2 = L.get(i, w - q), a3 = L.get(i - d, w - q);
@@ -786,11 +855,12 @@ template <int FMT>
 __device__ __forceinline__ Plane build_s32(const Job& j, const BitGeo& g, uint32_t* in,
                                            uint32_t* vb, uint32_t* s32buf, PassBox& pb) {
   const int RP = g.RP, Wv = g.Wv, R1 = g.R1, W1 = g.W1, ra = g.ra, wa = g.wa, pa = g.pa;
+  Team& tm = *pb.tm;
   // 1. input bits of rows [pa, rhi), words [wa-1, whi)
-  for_cells(RP, Wv, [&](int rr, int cc) {
+  for_cells(tm, RP, Wv, [&](int rr, int cc) {
     in[rr * Wv + cc] = input_word<FMT>(j, pa + rr, wa - 1 + cc);
   });
-  __syncthreads();
+  tm.barrier();
   // 2. vertical: V_32(i, w) = AND of the 32 rows ending at i, by doubling
   //    V_2k(i) = V_k(i) & V_k(i-k) over rows [pa, rhi) (5 passes, ping-pong
   //    between `in` and `vb`, ending in `vb`).  Rows above pa read as zeros,
@@ -800,11 +870,11 @@ __device__ __forceinline__ Plane build_s32(const Job& j, const BitGeo& g, uint32
     uint32_t* src = in;
     uint32_t* dst = vb;
     for (int k = 1; k < 32; k *= 2) {
-      for_cells(RP, Wv, [&](int rr, int cc) {
+      for_cells(tm, RP, Wv, [&](int rr, int cc) {
         const int e = rr * Wv + cc;
         dst[e] = rr >= k ? src[e] & src[e - k * Wv] : 0u;
       });
-      __syncthreads();
+      tm.barrier();
       uint32_t* t = src;
       src = dst;
       dst = t;
@@ -815,7 +885,7 @@ __device__ __forceinline__ Plane build_s32(const Job& j, const BitGeo& g, uint32
   Plane s32{s32buf, ra, wa, W1, 0, 0, 0, 0};
   int rmin = 0x7fffffff, rmax = -1, wmin = 0x7fffffff, wmax = -1;
   pb.begin();
-  for_cells(R1, W1, [&](int rr, int cc) {
+  for_cells(tm, R1, W1, [&](int rr, int cc) {
     const int vr = rr + (ra - pa);  // row of V_32 in its [pa, rhi) layout
     const uint32_t x = vb[vr * Wv + cc + 1], y = vb[vr * Wv + cc];
     unsigned long long z = ((unsigned long long)x << 32) | y;
@@ -851,21 +921,36 @@ __device__ __forceinline__ void pass_box_init(int (*s_box)[4]) {
   }
 }
 
-// Size-only.  The three planes live in shared memory when they fit in
-// `smem_words` words (small boxes: every pass then runs from shared memory),
-// else in the job's global scratch.
+// Size-only, by a team of `team_size` blocks (ranks 0..team_size-1, all
+// called with the same box; `sync` may be null only for a team of one).  When
+// the three planes fit in `smem_words` words of shared memory, rank 0 works
+// alone from shared memory and the other ranks return; otherwise the planes
+// live in the job's global scratch and the whole team shares every pass.
 template <int FMT>
 __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int clo, int chi,
-                                           uint32_t* smem, int64_t smem_words) {
+                                           uint32_t* smem, int64_t smem_words, int team_size,
+                                           int rank, TeamSync* sync) {
   __shared__ unsigned long long s_first;
   __shared__ int s_box[3][4];
-  PassBox pb{s_box, 0};
-  pass_box_init(s_box);
-  if (threadIdx.x == 0) s_first = ~0ull;
   const BitGeo g(rlo, rhi, clo, chi);
   const int wlo = g.wlo, whi = g.whi;
+  const bool fits = smem && 2 * (int64_t)g.RP * g.Wv + (int64_t)g.R1 * g.W1 <= smem_words;
+  const bool alone = fits || !sync || team_size <= 1;
+  if (alone && rank != 0) return;
+  Team tm{alone ? 1 : team_size, alone ? 0 : rank, alone ? nullptr : sync, &j.st->status, 0u,
+          false};
+  PassBox pb{s_box, 0, &tm};
+  pass_box_init(s_box);
+  if (threadIdx.x == 0) {
+    s_first = ~0ull;
+    if (!alone && rank == 0) {
+      box_reset(sync->box[0]);
+      sync->first = ~0ull;
+    }
+  }
+  unsigned long long* first = alone ? &s_first : &sync->first;
   uint32_t *buf0, *buf1, *buf2;  // V_32 then levels / S_32 on the grown box / input then levels
-  if (smem && 2 * (int64_t)g.RP * g.Wv + (int64_t)g.R1 * g.W1 <= smem_words) {
+  if (fits) {
     buf2 = smem;
     buf0 = smem + g.RP * g.Wv;
     buf1 = smem + 2 * g.RP * g.Wv;
@@ -907,11 +992,12 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
     if (!probe.empty()) lo = t; else hi = t;
   }
   // 5. witness: the first set bit of S_lo inside the box
-  grow_pass(cur, probe, rhi, whi, lo - a, j.n, false, &s_first, pb);
-  if (threadIdx.x == 0 && s_first != ~0ull) {
-    const unsigned long long idx = s_first;
-    atomicMax(&j.st->key, make_key((int32_t)lo, (int64_t)(idx / (unsigned long long)j.n),
-                                   (int64_t)(idx % (unsigned long long)j.n), j.n));
+  grow_pass(cur, probe, rhi, whi, lo - a, j.n, false, first, pb);
+  if (threadIdx.x == 0 && tm.rank == 0) {
+    const unsigned long long idx = *reinterpret_cast<volatile unsigned long long*>(first);
+    if (idx != ~0ull)
+      atomicMax(&j.st->key, make_key((int32_t)lo, (int64_t)(idx / (unsigned long long)j.n),
+                                     (int64_t)(idx % (unsigned long long)j.n), j.n));
   }
   __syncthreads();
 }
@@ -958,7 +1044,8 @@ template <int FMT>
 __device__ __forceinline__ void fixup_dp_levels(const Job& j, int rlo, int rhi, int clo, int chi,
                                                 uint32_t* smem, int64_t smem_words) {
   __shared__ int s_box[3][4];
-  PassBox pb{s_box, 0};
+  Team tm{1, 0, nullptr, &j.st->status, 0u, false};
+  PassBox pb{s_box, 0, &tm};
   pass_box_init(s_box);
   LevelTab* tab = reinterpret_cast<LevelTab*>(j.bits_scratch);
   uint32_t* base = j.bits_scratch + kTabWords;
@@ -1152,7 +1239,8 @@ __device__ __forceinline__ void fixup_job(const Job& j) {
 
 // Size-only fix-up of one matrix by bitplane growth, then its result.
 template <int FMT>
-__device__ __forceinline__ void fixup_bits_job(const Job& j, uint32_t* smem, int64_t smem_words) {
+__device__ __forceinline__ void fixup_bits_job(const Job& j, uint32_t* smem, int64_t smem_words,
+                                               int team_size, int rank, TeamSync* sync) {
   __shared__ int32_t sbox[4];
   if (threadIdx.x == 0) {
     sbox[0] = j.st->box[0];
@@ -1162,31 +1250,40 @@ __device__ __forceinline__ void fixup_bits_job(const Job& j, uint32_t* smem, int
   }
   __syncthreads();
   if (sbox[1] > sbox[0] && sbox[3] > sbox[2])
-    fixup_bits<FMT>(j, sbox[0], sbox[1], sbox[2], sbox[3], smem, smem_words);
+    fixup_bits<FMT>(j, sbox[0], sbox[1], sbox[2], sbox[3], smem, smem_words, team_size, rank,
+                    sync);
+  if (rank != 0) return;
   __syncthreads();
   finalize_job(j);
 }
 
+// One matrix: a team of gridDim.x blocks (`sync` zeroed before the launch when
+// there are several).
 template <int FMT>
-__global__ void __launch_bounds__(1024, 1) k_fixup_bits_one(const Job job, int64_t smem_words) {
+__global__ void __launch_bounds__(1024, 1) k_fixup_bits_one(const Job job, int64_t smem_words,
+                                                            TeamSync* sync) {
   extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
-  fixup_bits_job<FMT>(job, reinterpret_cast<uint32_t*>(ms_dyn_smem), smem_words);
+  fixup_bits_job<FMT>(job, reinterpret_cast<uint32_t*>(ms_dyn_smem), smem_words, (int)gridDim.x,
+                      (int)blockIdx.x, sync);
 }
 
-// Batch: every job with bitplane scratch (the others go to the strip fix-up).
+// Batch: one block per (matrix, rank) task, larger teams first; matrices
+// without bitplane scratch go to the strip fix-up.
+struct FixTask {
+  int32_t job, rank, size, pad;
+};
 constexpr int kBitsMixedThreads = 512;
 static __global__ void __launch_bounds__(kBitsMixedThreads, 2)
-    k_fixup_bits_mixed(const Job* __restrict__ jobs, int njobs, int64_t smem_words) {
+    k_fixup_bits_mixed(const Job* __restrict__ jobs, const FixTask* __restrict__ tasks,
+                       TeamSync* syncs, int64_t smem_words) {
   extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
-  const int jj = blockIdx.x;
-  if (jj >= njobs) return;
-  const Job job = jobs[jj];
-  if (!job.bits_scratch) return;
+  const FixTask t = tasks[blockIdx.x];
+  const Job job = jobs[t.job];
   uint32_t* smem = reinterpret_cast<uint32_t*>(ms_dyn_smem);
   if (job.fmt == MS_U8)
-    fixup_bits_job<MS_U8>(job, smem, smem_words);
+    fixup_bits_job<MS_U8>(job, smem, smem_words, t.size, t.rank, syncs + t.job);
   else
-    fixup_bits_job<MS_BITS32>(job, smem, smem_words);
+    fixup_bits_job<MS_BITS32>(job, smem, smem_words, t.size, t.rank, syncs + t.job);
 }
 
 template <int FMT, bool DPMAP>

@@ -123,6 +123,25 @@ def test_wide_matrix_automatic_lane_width(ctx):
     run_all_paths(ctx, a, check_map=True, pads=(0, 1))
 
 
+def test_large_boxes_shared_by_block_teams(ctx):
+    """Large flagged boxes are shared by teams of blocks (one matrix alone,
+    and several in a batch): side and witness against the oracle."""
+    mats, exps = [], []
+    for t, (m, n, s) in enumerate([(6000, 6000, 1500), (2048, 2048, 1400), (1800, 2000, 900)]):
+        a = gen.bernoulli_u8(m, n, 0.9, seed=9100 + t)
+        r0, c0 = (m - s) // 3, (n - s) // 2
+        a[r0:r0 + s, c0:c0 + s] = 1
+        exp = list(oracle.dp(a, want_map=False)[0]) + [0]
+        assert exp[0] >= s
+        x = to_dev(a)
+        assert ctx.max_square(x).cpu().tolist() == exp, (m, n, "u8")
+        w = bits_dev(a, n, pad=1)
+        assert ctx.max_square(w, n=n).cpu().tolist() == exp, (m, n, "bits")
+        mats += [x, (w, n)]
+        exps += [exp, exp]
+    assert ctx.batch(mats).cpu().tolist() == exps
+
+
 def test_squares_on_tile_edges(ctx):
     ctx.set_tuning(band_rows=64)
     try:
