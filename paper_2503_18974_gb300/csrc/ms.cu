@@ -786,10 +786,24 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     }
   }
   {
+    // groups stay contiguous in the queue (warps running at the same time
+    // mostly execute one lane-width variant, which keeps the instruction
+    // cache warm), the group with the longest tiles first, longest first
+    // within each group
     std::vector<size_t> idx(tasks.size());
     for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
-    std::stable_sort(idx.begin(), idx.end(),
-                     [&](size_t a, size_t b) { return task_steps[a] > task_steps[b]; });
+    std::vector<int> group_of(tasks.size()), group_max(2 * 64, 0);
+    for (size_t k = 0; k < tasks.size(); ++k) {
+      const Job& ja = jobs[tasks[k].job_a];
+      group_of[k] = ja.fmt * 64 + ja.P;
+      group_max[group_of[k]] = std::max(group_max[group_of[k]], task_steps[k]);
+    }
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+      const int ga = group_of[a], gb = group_of[b];
+      if (ga != gb)
+        return group_max[ga] != group_max[gb] ? group_max[ga] > group_max[gb] : ga > gb;
+      return task_steps[a] > task_steps[b];
+    });
     std::vector<ms::PairTask> sorted(tasks.size());
     for (size_t k = 0; k < idx.size(); ++k) sorted[k] = tasks[idx[k]];
     tasks.swap(sorted);
