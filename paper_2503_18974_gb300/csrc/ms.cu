@@ -362,9 +362,15 @@ ms_status ensure_workspace(ms_ctx* ctx, int64_t njobs, int64_t carry, int64_t pr
 
 // ---- launches --------------------------------------------------------------
 
+// Size-only calls on matrices below this many cells finish inside the tile
+// launch (its last block runs the fix-up and writes the result): one launch
+// per call, where the separate fix-up launch would cost more than the work.
+constexpr int64_t kFusedFinishCells = (int64_t)1 << 24;
+
 template <int FMT, bool DPMAP>
 cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   const int64_t ntiles = tiles_of(j);
+  const int fuse = (!DPMAP && j.bits_scratch && ntiles > 0 && j.m * j.n < kFusedFinishCells) ? 1 : 0;
   if (ntiles > 0) {
     ProfScope ps(ctx, s, kProfTile);
     const int64_t warps = (ntiles + 1) / 2;
@@ -379,7 +385,7 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   case PP:                                                                              \
     if (allow_smem((const void*)ms::k_tiles_one<PP, FMT, DPMAP>, sm) != cudaSuccess)    \
       return cudaGetLastError();                                                        \
-    ms::k_tiles_one<PP, FMT, DPMAP><<<grid, 32 * wpb, sm, s>>>(j, ntiles);              \
+    ms::k_tiles_one<PP, FMT, DPMAP><<<grid, 32 * wpb, sm, s>>>(j, ntiles, fuse);        \
     break;
       MS_LAUNCH_TILES(1)
       MS_LAUNCH_TILES(2)
@@ -391,7 +397,7 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
 #undef MS_LAUNCH_TILES
     }
   }
-  {
+  if (!fuse) {
     ProfScope ps(ctx, s, kProfFixup);
     if (!DPMAP && j.bits_scratch) {
       // size-only: bitplane growth in the flagged box, planes in shared

@@ -35,7 +35,7 @@ struct JobState {
   unsigned long long key;  // (side << 40) | (kKeyMask - (row*n + col)), atomicMax
   int32_t box[4];          // unresolved region: row lo, row hi, col lo, col hi
   int32_t status;          // ms_status of device-side problems
-  int32_t pad;
+  int32_t done;            // tile-pass blocks finished (fused size-only finish)
 };
 
 struct Job {

@@ -585,13 +585,6 @@ static __global__ void __launch_bounds__(256, 2) k_batch_tiles(const Job* __rest
   }
 }
 
-// Every variant fits 128 registers without spills, so two 256-thread blocks
-// share an SM.  Single matrix: the job travels as a kernel parameter.
-template <int P, int FMT, bool DPMAP>
-__global__ void __launch_bounds__(256, 2) k_tiles_one(const Job job, int64_t ntiles) {
-  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  tile_pass_warp<P, FMT, DPMAP>(&job, 1, ntiles, w);
-}
 
 // ---- fix-up and result ------------------------------------------------------
 
@@ -1176,6 +1169,7 @@ __device__ __forceinline__ void finalize_job(const Job& j) {
     st->box[2] = 0x7fffffff;
     st->box[3] = -1;
     st->status = 0;
+    st->done = 0;
   }
 }
 
@@ -1243,10 +1237,11 @@ __device__ __forceinline__ void fixup_bits_job(const Job& j, uint32_t* smem, int
                                                int team_size, int rank, TeamSync* sync) {
   __shared__ int32_t sbox[4];
   if (threadIdx.x == 0) {
-    sbox[0] = j.st->box[0];
-    sbox[1] = j.st->box[1];
-    sbox[2] = j.st->box[2];
-    sbox[3] = j.st->box[3];
+    const volatile int32_t* b = j.st->box;
+    sbox[0] = b[0];
+    sbox[1] = b[1];
+    sbox[2] = b[2];
+    sbox[3] = b[3];
   }
   __syncthreads();
   if (sbox[1] > sbox[0] && sbox[3] > sbox[2])
@@ -1301,6 +1296,36 @@ __global__ void __launch_bounds__(kFixWarps * 32, 1) k_fixup_one(const Job job) 
   fixup_job<FMT, DPMAP>(job);
 }
 
+// Every variant fits 128 registers without spills, so two 256-thread blocks
+// share an SM.  Single matrix: the job travels as a kernel parameter.
+//
+// fuse != 0 (size-only, small matrices): the last block to finish also
+// finishes the matrix -- the bitplane fix-up of its box, if any, from the
+// block's ring memory or the job's scratch, then the result -- so that one
+// launch does the whole call.
+template <int P, int FMT, bool DPMAP>
+__global__ void __launch_bounds__(256, 2) k_tiles_one(const Job job, int64_t ntiles, int fuse) {
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  tile_pass_warp<P, FMT, DPMAP>(&job, 1, ntiles, w);
+  if constexpr (!DPMAP) {
+    if (fuse) {
+      __shared__ int s_last;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();  // this block's key and box updates before its ticket
+        s_last = atomicAdd(&job.st->done, 1) == (int)gridDim.x - 1;
+        if (s_last) __threadfence();
+      }
+      __syncthreads();
+      if (s_last) {
+        extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
+        fixup_bits_job<FMT>(job, reinterpret_cast<uint32_t*>(ms_dyn_smem),
+                            (int64_t)(blockDim.x >> 5) * kRingWarpBytes / 4, 1, 0, nullptr);
+      }
+    }
+  }
+}
+
 static __global__ void k_init_states(JobState* st, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
@@ -1310,7 +1335,7 @@ static __global__ void k_init_states(JobState* st, int n) {
     st[i].box[2] = 0x7fffffff;
     st[i].box[3] = -1;
     st[i].status = 0;
-    st[i].pad = 0;
+    st[i].done = 0;
   }
 }
 

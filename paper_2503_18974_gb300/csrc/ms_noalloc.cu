@@ -62,7 +62,7 @@ __global__ void k_noalloc_reset(int nstrips) {
     st->box[2] = 0x7fffffff;
     st->box[3] = -1;
     st->status = 0;
-    st->pad = 0;
+    st->done = 0;
   }
   for (int i = threadIdx.x; i < nstrips; i += blockDim.x) progress[i] = 0;
 }
