@@ -53,6 +53,9 @@ def _l():
             f = getattr(lib, name)
             f.restype = ctypes.c_int
             f.argtypes = [_vp, _i64, _i64, _i64, ctypes.POINTER(_Result)]
+        lib.oracle_all_max.restype = ctypes.c_int
+        lib.oracle_all_max.argtypes = [_vp, _i64, _i64, _i64, _vp, _i64,
+                                       ctypes.POINTER(_i64), ctypes.POINTER(_Result)]
         lib.oracle_erode.restype = ctypes.c_int
         lib.oracle_erode.argtypes = [_vp, _i64, _i64, _i64, _i64, _vp, _i64]
         _lib = lib
@@ -127,6 +130,21 @@ def brute(a: np.ndarray, n: int | None = None):
     res = _Result()
     _check(_l().oracle_brute(a.ctypes.data, m, n, ld, ctypes.byref(res)), "oracle_brute")
     return _tuple(res)
+
+
+def all_max(a: np.ndarray, n: int | None = None):
+    """Every bottom-right corner of a largest all-ones square, row-major.
+    Returns ((side, row, col), int32 array of shape (count, 2))."""
+    a, m, n, ld = _mat(a, n)
+    res = _Result()
+    cnt = _i64(0)
+    _check(_l().oracle_all_max(a.ctypes.data, m, n, ld, None, 0, ctypes.byref(cnt),
+                               ctypes.byref(res)), "oracle_all_max")
+    out = np.zeros((max(cnt.value, 1), 2), dtype=np.int32)
+    if cnt.value:
+        _check(_l().oracle_all_max(a.ctypes.data, m, n, ld, out.ctypes.data, cnt.value,
+                                   ctypes.byref(cnt), ctypes.byref(res)), "oracle_all_max")
+    return _tuple(res), out[:cnt.value]
 
 
 def erode(a: np.ndarray, t: int, n: int | None = None) -> np.ndarray:

@@ -214,3 +214,47 @@ int oracle_erode(const uint8_t* v, int64_t m, int64_t n, int64_t ld, int64_t t, 
     }
   return 0;
 }
+
+/* K from the O(n)-space recurrence, then a second pass over the same rows
+ * collects every cell whose dp equals K, in row-major order. */
+int oracle_all_max(const uint8_t* v, int64_t m, int64_t n, int64_t ld, int32_t* corners,
+                   int64_t cap, int64_t* count, oracle_result* out) {
+  *count = 0;
+  if (oracle_dp_rows(v, m, n, ld, out) != 0) return -1;
+  const int32_t K = out->side;
+  if (K == 0) return 0;
+  int32_t* prev = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+  int32_t* cur = (int32_t*)calloc((size_t)n, sizeof(int32_t));
+  if (!prev || !cur) {
+    free(prev);
+    free(cur);
+    return -1;
+  }
+  for (int64_t i = 0; i < m; ++i) {
+    for (int64_t j = 0; j < n; ++j) {
+      int32_t d = 0;
+      if (V(i, j)) {
+        int32_t up = prev[j];
+        int32_t left = (j > 0) ? cur[j - 1] : 0;
+        int32_t diag = (j > 0) ? prev[j - 1] : 0;
+        int32_t mn = up < left ? up : left;
+        mn = mn < diag ? mn : diag;
+        d = mn + 1;
+      }
+      cur[j] = d;
+      if (d == K) {
+        if (*count < cap) {
+          corners[2 * *count] = (int32_t)i;
+          corners[2 * *count + 1] = (int32_t)j;
+        }
+        ++*count;
+      }
+    }
+    int32_t* t = prev;
+    prev = cur;
+    cur = t;
+  }
+  free(prev);
+  free(cur);
+  return 0;
+}

@@ -25,6 +25,7 @@
  *   oracle_freq_dpmap  pinned: equals oracle_dp's map, closed forms
  *   oracle_brute       pinned: independent numpy enumeration, closed forms
  *   oracle_erode       pinned: equals [dp >= t], closed forms
+ *   oracle_all_max     pinned: brute-force enumeration, closed forms
  */
 #ifndef MS_ORACLE_H
 #define MS_ORACLE_H
@@ -66,6 +67,14 @@ int oracle_brute(const uint8_t* v, int64_t m, int64_t n, int64_t ld, oracle_resu
  * bit-packed erosion path. */
 int oracle_erode(const uint8_t* v, int64_t m, int64_t n, int64_t ld, int64_t t, uint8_t* s,
                  int64_t ld_s);
+
+/* All maximal squares (the paper's "all maximal squares" reading, Sec. 3.4
+ * and Sec. 6): the bottom-right corner of every all-ones square of the largest
+ * side K, i.e. every (i, j) with dp[i][j] == K, in row-major order.  Writes up
+ * to cap (row, col) pairs to corners[2*k], [2*k+1] and the total number to
+ * *count (none when K == 0).  Returns 0, or -1 on allocation failure. */
+int oracle_all_max(const uint8_t* v, int64_t m, int64_t n, int64_t ld, int32_t* corners,
+                   int64_t cap, int64_t* count, oracle_result* out);
 
 #ifdef __cplusplus
 }

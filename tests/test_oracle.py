@@ -308,3 +308,60 @@ def test_generated_config_shapes_small():
     assert len(set(res.values())) == 1
     (K, r, c) = res["dp"]
     assert 3 <= K <= 10 and r >= 0 and c >= 0
+
+
+# ------------------------------------------------------ all maximal squares -
+
+def np_all_max(a):
+    """Independent enumeration: K by integral images, then every top-left
+    (r, c) whose K x K window sums to K*K, reported as its bottom-right corner
+    (r + K - 1, c + K - 1), sorted row-major."""
+    x = (np.asarray(a) != 0).astype(np.int64)
+    m, n = x.shape
+    K = np_brute(x)[0]
+    if K == 0:
+        return 0, []
+    I = np.zeros((m + 1, n + 1), dtype=np.int64)
+    I[1:, 1:] = x.cumsum(0).cumsum(1)
+    win = I[K:, K:] - I[:-K, K:] - I[K:, :-K] + I[:-K, :-K]
+    rs, cs = np.nonzero(win == K * K)
+    return K, sorted((int(r) + K - 1, int(c) + K - 1) for r, c in zip(rs, cs))
+
+
+def test_all_max_against_enumeration():
+    rng = np.random.default_rng(77)
+    for trial in range(400):
+        m, n = int(rng.integers(1, 13)), int(rng.integers(1, 13))
+        a = (rng.random((m, n)) < rng.uniform(0.3, 0.95)).astype(np.uint8)
+        (K, r, c), corners = oracle.all_max(a)
+        K2, want = np_all_max(a)
+        assert K == K2
+        assert [tuple(p) for p in corners.tolist()] == want  # row-major order
+        if K:
+            assert (r, c) == want[0]
+    # every 3 x 3 matrix
+    for bits in range(1 << 9):
+        a = np.array([(bits >> k) & 1 for k in range(9)], dtype=np.uint8).reshape(3, 3)
+        K, want = np_all_max(a)
+        assert [tuple(p) for p in oracle.all_max(a)[1].tolist()] == want
+
+
+def test_all_max_closed_forms():
+    # all ones, m >= n: the n-squares stacked down the only column band
+    for m, n in [(1, 1), (5, 5), (9, 4), (4, 9), (30, 7)]:
+        (K, _, _), corners = oracle.all_max(np.ones((m, n), dtype=np.uint8))
+        s = min(m, n)
+        assert K == s
+        want = [(i, j) for i in range(s - 1, m) for j in range(s - 1, n)]
+        assert [tuple(p) for p in corners.tolist()] == want
+        assert len(want) == (m - s + 1) * (n - s + 1)
+    # all zeros and empty: no square at all
+    assert oracle.all_max(np.zeros((6, 7), dtype=np.uint8))[1].shape == (0, 2)
+    assert oracle.all_max(np.zeros((0, 7), dtype=np.uint8))[1].shape == (0, 2)
+    # two disjoint planted squares of the same largest side in a sparse field
+    a = np.zeros((40, 50), dtype=np.uint8)
+    a[3:11, 5:13] = 1
+    a[20:28, 30:38] = 1
+    (K, r, c), corners = oracle.all_max(a)
+    assert K == 8 and [tuple(p) for p in corners.tolist()] == [(10, 12), (27, 37)]
+    assert (r, c) == (10, 12)
