@@ -95,6 +95,20 @@ ms_status ms_max_square(ms_ctx* ctx, const ms_matrix* in, ms_result* out_dev, ms
 ms_status ms_dp_map(ms_ctx* ctx, const ms_matrix* in, int32_t* dp_dev, int64_t ld_dp,
                     ms_result* out_dev, ms_stream_t s);
 
+/* All largest squares (the paper's "all maximal squares", Sec. 3.4 and
+ * Sec. 6): the bottom-right corner of every all-ones square of the largest
+ * side K, i.e. every cell with dp == K.  `out_dev` receives the same ms_result
+ * as ms_max_square; `count_dev` (one int64, device memory) the number of
+ * such corners, which may exceed `capacity`; `corners_dev` (device memory,
+ * room for `capacity` pairs; may be null when capacity is 0) the first
+ * min(count, capacity) of them as int32 (row, col) pairs, in unspecified
+ * order (the set itself is unique).  Nothing is listed when K == 0.
+ * MS_U8 and MS_BITS32 input (always through the tile kernels).  Returns
+ * MS_ERR_OOM if the fix-up bitplane scratch cannot be allocated. */
+ms_status ms_all_max_squares(ms_ctx* ctx, const ms_matrix* in, int32_t* corners_dev,
+                             int64_t capacity, int64_t* count_dev, ms_result* out_dev,
+                             ms_stream_t s);
+
 /* Side and witness for `count` matrices of possibly different shapes and
  * formats in one pass: the descriptors are read from HOST memory (ins_host),
  * the results go to outs_dev[0..count-1] in device memory.  Work from all

@@ -95,7 +95,8 @@ class ServerStats(ctypes.Structure):
 
 _lib = None
 
-EXPORTS = ("ms_create", "ms_destroy", "ms_max_square", "ms_dp_map", "ms_batch",
+EXPORTS = ("ms_create", "ms_destroy", "ms_max_square", "ms_dp_map", "ms_all_max_squares",
+           "ms_batch",
            "ms_status_string", "ms_set_tuning", "ms_get_tuning", "ms_profile_start",
            "ms_profile_stop", "ms_autotune", "ms_max_square_noalloc", "ms_server_create",
            "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats_get",
@@ -118,6 +119,8 @@ def lib():
         L.ms_max_square.argtypes = [vp, ctypes.POINTER(_Matrix), vp, vp]
         L.ms_dp_map.restype = ctypes.c_int
         L.ms_dp_map.argtypes = [vp, ctypes.POINTER(_Matrix), vp, i64, vp, vp]
+        L.ms_all_max_squares.restype = ctypes.c_int
+        L.ms_all_max_squares.argtypes = [vp, ctypes.POINTER(_Matrix), vp, i64, vp, vp, vp]
         L.ms_batch.restype = ctypes.c_int
         L.ms_batch.argtypes = [vp, ctypes.POINTER(_Matrix), ctypes.c_int32, vp, vp]
         L.ms_status_string.restype = ctypes.c_char_p
@@ -249,6 +252,26 @@ class MaxSquare:
         _check(lib().ms_max_square(self._h, ctypes.byref(desc), out.data_ptr(),
                                    _stream_ptr(stream)), "ms_max_square")
         return out
+
+    def all_max_squares(self, x, n: int | None = None, fmt: int | None = None,
+                        capacity: int = 1024, stream=None):
+        """Every bottom-right corner of a largest all-ones square.  Returns
+        (result tensor [side, row, col, status], int32 (count, 2) corners, in
+        unspecified order).  Calls again with room for all of them when the
+        first capacity was too small."""
+        import torch
+        desc = describe(x, n, fmt)
+        out = torch.empty(4, dtype=torch.int32, device=x.device)
+        count = torch.zeros(1, dtype=torch.int64, device=x.device)
+        while True:
+            corners = torch.empty((max(capacity, 1), 2), dtype=torch.int32, device=x.device)
+            _check(lib().ms_all_max_squares(self._h, ctypes.byref(desc), corners.data_ptr(),
+                                            capacity, count.data_ptr(), out.data_ptr(),
+                                            _stream_ptr(stream)), "ms_all_max_squares")
+            c = int(count.item())
+            if c <= capacity:
+                return out, corners[:c]
+            capacity = c
 
     def dp_map(self, x, n: int | None = None, fmt: int | None = None, dp=None, out=None,
                stream=None):

@@ -432,6 +432,42 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Second pass of the all-largest-squares call (lists corners when the
+// largest side is at most the halo).
+cudaError_t launch_emit(ms_ctx* ctx, const Job& j, cudaStream_t s) {
+  const int64_t ntiles = tiles_of(j);
+  if (ntiles <= 0) return cudaSuccess;
+  ProfScope ps(ctx, s, kProfOther);
+  const int64_t warps = (ntiles + 1) / 2;
+  const int wpb = (int)std::min<int64_t>(kTileThreads / 32, (warps + ctx->sms - 1) / ctx->sms);
+  const unsigned grid = (unsigned)((warps + wpb - 1) / wpb);
+  const size_t sm = ring_bytes(32 * wpb);
+  switch (j.fmt * 64 + j.P) {
+#define MS_LAUNCH_EMIT(FF, PP)                                                            \
+  case FF * 64 + PP:                                                                      \
+    if (allow_smem((const void*)ms::k_tiles_emit<PP, FF>, sm) != cudaSuccess)            \
+      return cudaGetLastError();                                                          \
+    ms::k_tiles_emit<PP, FF><<<grid, 32 * wpb, sm, s>>>(j, ntiles);                       \
+    break;
+    MS_LAUNCH_EMIT(MS_U8, 1)
+    MS_LAUNCH_EMIT(MS_U8, 2)
+    MS_LAUNCH_EMIT(MS_U8, 4)
+    MS_LAUNCH_EMIT(MS_U8, 8)
+    MS_LAUNCH_EMIT(MS_U8, 16)
+    MS_LAUNCH_EMIT(MS_U8, 32)
+    MS_LAUNCH_EMIT(MS_BITS32, 1)
+    MS_LAUNCH_EMIT(MS_BITS32, 2)
+    MS_LAUNCH_EMIT(MS_BITS32, 4)
+    MS_LAUNCH_EMIT(MS_BITS32, 8)
+    MS_LAUNCH_EMIT(MS_BITS32, 16)
+    MS_LAUNCH_EMIT(MS_BITS32, 32)
+#undef MS_LAUNCH_EMIT
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // ---- bit-packed size-only search ---------------------------------------------
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -547,8 +583,15 @@ ms_status run_bits_search(ms_ctx* ctx, const ms_matrix* in, ms_result* out_dev, 
   return cuda_status(cudaGetLastError());
 }
 
+// Where the all-largest-squares call lists its corners.
+struct CornerOut {
+  int32_t* corners;
+  int64_t cap;
+  unsigned long long* count;
+};
+
 ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_dp,
-                     ms_result* out_dev, cudaStream_t s) {
+                     ms_result* out_dev, cudaStream_t s, const CornerOut* co = nullptr) {
   ms_status st = check_matrix(in);
   if (st != MS_OK) return st;
   if (!out_dev) return MS_ERR_INVALID;
@@ -557,7 +600,7 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   }
   DeviceGuard g(ctx->device);
   const ms_tuning tune = effective_tuning(ctx, in, 1, false);
-  if (!dp && bits_search_applies(tune, in)) return run_bits_search(ctx, in, out_dev, s);
+  if (!dp && !co && bits_search_applies(tune, in)) return run_bits_search(ctx, in, out_dev, s);
   Job j = plan_job(tune, in, dp != nullptr, 32, ctx->sms);
   st = ensure_workspace(ctx, 1, ms::carry_words(j.m, j.strips_fix), j.strips_fix, s);
   if (st != MS_OK) return st;
@@ -575,12 +618,20 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   j.st = ctx->d_states;
   j.carry = ctx->d_carry;
   j.progress = ctx->d_progress;
+  if (co) {
+    // corners of squares above the halo are listed by the bitplane fix-up
+    if (!j.bits_scratch && j.m > 0 && j.n > 0) return MS_ERR_OOM;
+    j.corners = co->corners;
+    j.corners_cap = co->cap;
+    j.corners_count = co->count;
+  }
   cudaError_t e;
   if (j.fmt == MS_U8)
     e = dp ? launch_one_fmt<MS_U8, true>(ctx, j, s) : launch_one_fmt<MS_U8, false>(ctx, j, s);
   else
     e = dp ? launch_one_fmt<MS_BITS32, true>(ctx, j, s)
            : launch_one_fmt<MS_BITS32, false>(ctx, j, s);
+  if (e == cudaSuccess && co) e = launch_emit(ctx, j, s);
   return cuda_status(e);
 }
 
@@ -710,6 +761,19 @@ ms_status ms_dp_map(ms_ctx* ctx, const ms_matrix* in, int32_t* dp_dev, int64_t l
   if (!ctx || !in) return MS_ERR_INVALID;
   if (!dp_dev && in->m > 0 && in->n > 0) return MS_ERR_INVALID;
   return run_single(ctx, in, dp_dev, ld_dp, out_dev, reinterpret_cast<cudaStream_t>(s));
+}
+
+extern "C" ms_status ms_all_max_squares(ms_ctx* ctx, const ms_matrix* in, int32_t* corners_dev,
+                                        int64_t capacity, int64_t* count_dev,
+                                        ms_result* out_dev, ms_stream_t s) {
+  if (!ctx || !count_dev || capacity < 0 || (capacity > 0 && !corners_dev)) return MS_ERR_INVALID;
+  ms_status st = check_matrix(in);
+  if (st != MS_OK) return st;
+  DeviceGuard g(ctx->device);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(s);
+  if (cudaMemsetAsync(count_dev, 0, sizeof(int64_t), cs) != cudaSuccess) return MS_ERR_CUDA;
+  const CornerOut co{corners_dev, capacity, reinterpret_cast<unsigned long long*>(count_dev)};
+  return run_single(ctx, in, nullptr, 0, out_dev, cs, &co);
 }
 
 ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_result* outs_dev,

@@ -58,7 +58,19 @@ struct Job {
   int32_t strips_fix;      // capacity of carry/progress in strips
   int32_t test_hold;       // test hook: the first fix-up strip never publishes carries
   uint32_t* bits_scratch;  // size-only fix-up bitplanes (3 x m x (ceil(n/32)+2) words), or null
+  int32_t* corners;        // all largest squares: (row, col) pairs, or null
+  int64_t corners_cap;     // pairs that fit in corners
+  unsigned long long* corners_count;  // corners found (may exceed the capacity)
 };
+
+// Appends (i, c) to the job's list of largest-square corners.
+__device__ __forceinline__ void emit_corner(const Job& j, int64_t i, int64_t c) {
+  const unsigned long long k = atomicAdd(j.corners_count, 1ull);
+  if ((int64_t)k < j.corners_cap) {
+    j.corners[2 * k] = (int32_t)i;
+    j.corners[2 * k + 1] = (int32_t)c;
+  }
+}
 
 // Fix-up strip carries: one uint16 per window row and strip, each strip's
 // rows padded to a multiple of 8 so that 8 rows load as one 16-byte vector.

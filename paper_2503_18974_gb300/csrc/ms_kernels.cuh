@@ -269,11 +269,15 @@ __device__ __forceinline__ void store_dp(int32_t* p, const uint32_t* Ap, uint32_
 // Two independent tiles (low and high 16-bit halves), lanes skewed by a row.
 // Mode 0: tile pass (zero carries on the window edges).  Mode 1: a fix-up
 // strip taking its left carries from `io` and publishing its right ones.
-template <int P, int FMT, bool DPMAP, int MODE>
+//
+// EMIT (second pass of the all-largest-squares call, largest side emitK <=
+// kHalo known): every counted cell with dp == emitK is appended to ej's list.
+template <int P, int FMT, bool DPMAP, int MODE, bool EMIT = false>
 __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_t* dpa,
                                           int64_t lda, int dpa_al, int32_t* dpb, int64_t ldb,
                                           int dpb_al, const StripIO& io, Best& ba, Best& bb,
-                                          uint32_t ring) {
+                                          uint32_t ring, const Job* ej = nullptr,
+                                          uint32_t emitK = 0) {
   const int lane = threadIdx.x & 31;
   constexpr uint32_t kB2 = kBias * 0x10001u;
   constexpr int D = RingGeom<P, FMT>::kDepth;  // rows of input in flight per lane
@@ -431,6 +435,18 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
             bb.col = (int32_t)(colb + kk);
           }
           best2 = vmax2(d2, best2);
+        }
+        if constexpr (EMIT) {
+          const uint32_t km1 = (emitK - 1u) * 0x10001u;
+          if (vmax2(d2, km1) != km1) {  // a counted cell of this row reaches emitK
+            const bool elo = (d2 & 0xffffu) >= emitK, ehi = (d2 >> 16) >= emitK;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+              const uint32_t dk = I2 - Ap[k];
+              if (elo && (dk & 0xffffu) == emitK) emit_corner(*ej, ta.wr0 + ir, cola + k);
+              if (ehi && (dk >> 16) == emitK) emit_corner(*ej, tb.wr0 + ir, colb + k);
+            }
+          }
         }
         // rows and lane chunks holding a value above the halo: the fix-up box
         if (vmax2(d2, kHalo2) != kHalo2) {
@@ -782,7 +798,7 @@ struct PassBox {
 // receives the smallest row-major index of a set bit.
 __device__ __forceinline__ void grow_pass(const Plane& L, Plane& O, int o_r1, int o_w1, int d,
                                           int64_t n, bool write, unsigned long long* first,
-                                          PassBox& pb) {
+                                          PassBox& pb, const Job* emit = nullptr) {
   const int q = d >> 5, r = d & 31;
   const int r0 = max(L.ar0, O.r0), r1 = min(L.ar1, o_r1);
   const int w0 = max(L.aw0, O.w0), w1 = min(L.aw1, o_w1);
@@ -812,6 +828,9 @@ __device__ __forceinline__ void grow_pass(const Plane& L, Plane& O, int o_r1, in
                                         (unsigned long long)(__ffs(v) - 1);
         f = cand < f ? cand : f;
       }
+      if (emit)
+        for (uint32_t b = v; b; b &= b - 1)
+          emit_corner(*emit, i, 32 * (int64_t)w + (__ffs(b) - 1));
     }
   });
   if (first && f != ~0ull) atomicMin(first, f);
@@ -984,8 +1003,9 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
     grow_pass(cur, probe, rhi, whi, t - a, j.n, false, nullptr, pb);
     if (!probe.empty()) lo = t; else hi = t;
   }
-  // 5. witness: the first set bit of S_lo inside the box
-  grow_pass(cur, probe, rhi, whi, lo - a, j.n, false, first, pb);
+  // 5. witness: the first set bit of S_lo inside the box (and, for the
+  //    all-largest-squares call, every set bit: all of them lie in the box)
+  grow_pass(cur, probe, rhi, whi, lo - a, j.n, false, first, pb, j.corners_count ? &j : nullptr);
   if (threadIdx.x == 0 && tm.rank == 0) {
     const unsigned long long idx = *reinterpret_cast<volatile unsigned long long*>(first);
     if (idx != ~0ull)
@@ -1324,6 +1344,26 @@ __global__ void __launch_bounds__(256, 2) k_tiles_one(const Job job, int64_t nti
       }
     }
   }
+}
+
+// Second pass of the all-largest-squares call: when the largest side K
+// (written by the first pass) is at most the halo, every K-square corner is a
+// counted cell of some tile with an exact window value; recompute the tiles
+// and list those cells.  (Larger K: the box fix-up of the first pass listed
+// them.)  Publishes nothing to the matrix state.
+template <int P, int FMT>
+__global__ void __launch_bounds__(256, 2) k_tiles_emit(const Job job, int64_t ntiles) {
+  const int K = *reinterpret_cast<const volatile int32_t*>(&job.out->side);
+  if (K <= 0 || K > kHalo) return;
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t t_a = 2 * w, t_b = 2 * w + 1;
+  if (t_a >= ntiles) return;
+  const Tile ga = tile_of(job, t_a);
+  const Tile gb = t_b < ntiles ? tile_of(job, t_b) : empty_tile();
+  StripIO io{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+  Best ba, bb;
+  run_tiles<P, FMT, false, 0, true>(ga, gb, nullptr, 0, 0, nullptr, 0, 0, io, ba, bb,
+                                    warp_ring(), &job, (uint32_t)K);
 }
 
 static __global__ void k_init_states(JobState* st, int n) {

@@ -57,6 +57,10 @@ def test_null_arguments_rejected_without_gpu(libms):
     libms.ms_destroy.restype = ctypes.c_int
     libms.ms_destroy.argtypes = [ctypes.c_void_p]
     assert libms.ms_destroy(None) == 1
+    libms.ms_all_max_squares.restype = ctypes.c_int
+    libms.ms_all_max_squares.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int64] + \
+        [ctypes.c_void_p] * 3
+    assert libms.ms_all_max_squares(None, None, None, 0, None, None, None) == 1
 
 
 def test_python_binding_imports_and_fails_loudly_without_library(tmp_path, monkeypatch):
