@@ -185,6 +185,8 @@ typedef struct {
   int64_t peak_bytes;      /* largest arena use seen (never above the budget) */
   int32_t peak_inflight;   /* largest number of batches on the device at once */
   int32_t reserved;
+  double host_batch_s;     /* scheduler time spent planning and launching batches */
+  double host_copy_s;      /* scheduler time spent issuing input copies */
 } ms_server_stats;
 
 ms_status ms_server_create(ms_server** out, int device, const ms_server_config* cfg);

@@ -90,7 +90,8 @@ class Completion(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("peak_bytes", ctypes.c_int64),
-                ("peak_inflight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("peak_inflight", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("host_batch_s", ctypes.c_double), ("host_copy_s", ctypes.c_double)]
 
 
 _lib = None
@@ -343,6 +344,7 @@ class Server:
                "ms_server_create")
         self._h = h
         self._keep = {}
+        self._rid = ctypes.c_uint64()
 
     def submit(self, a, n: int | None = None, fmt: int | None = None, t_arrival: float = -1.0,
                keep=None) -> int:
@@ -353,6 +355,15 @@ class Server:
         _check(lib().ms_server_submit(self._h, ctypes.byref(desc), t_arrival, ctypes.byref(rid)),
                "ms_server_submit")
         self._keep[rid.value] = a if keep is None else keep
+        return rid.value
+
+    def submit_desc(self, desc: "_Matrix", t_arrival: float = -1.0) -> int:
+        """Submit a prebuilt descriptor (from host_describe) whose host memory
+        the caller keeps alive until completion: the low-overhead path for
+        load generators."""
+        rid = self._rid
+        _check(lib().ms_server_submit(self._h, ctypes.byref(desc), t_arrival, ctypes.byref(rid)),
+               "ms_server_submit")
         return rid.value
 
     def poll(self, max_n: int = 4096) -> list:
@@ -376,7 +387,7 @@ class Server:
         st = ServerStats()
         _check(lib().ms_server_stats_get(self._h, ctypes.byref(st)), "ms_server_stats_get")
         return {k: getattr(st, k) for k in ("submitted", "completed", "batches", "peak_bytes",
-                                            "peak_inflight")}
+                                            "peak_inflight", "host_batch_s", "host_copy_s")}
 
     def close(self) -> None:
         if getattr(self, "_h", None):

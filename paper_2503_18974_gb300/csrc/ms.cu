@@ -196,12 +196,16 @@ int choose_P(int64_t m, int64_t n, bool dp, int32_t forced, int max_P, int sms) 
   if (forced > 1 || (forced == 1 && n <= 32)) return std::min(forced, max_P);
   if (forced == 1) return 2;
   if (n <= 32) return 1;
-  if (n <= 64) return 2;
-  if (n <= 128) return 4;
-  if (n <= 256) return 8;
   const int top = std::min(dp ? 16 : 32, max_P);
-  if (sms == 0) return std::min(16, top);
-  int best = std::min(16, top);
+  if (sms == 0) {
+    if (n <= 64) return 2;
+    if (n <= 128) return 4;
+    if (n <= 256) return 8;
+    return std::min(16, top);
+  }
+  int cover = 2;  // the narrowest tile covering the matrix, at most the default
+  while (cover < 16 && 32 * cover < n) cover *= 2;
+  int best = std::min(cover, top);
   double best_cost = tile_cost(m, n, best, sms);
   for (int P = 2; P <= top; P *= 2) {
     const double c = tile_cost(m, n, P, sms);
@@ -362,15 +366,19 @@ ms_status ensure_workspace(ms_ctx* ctx, int64_t njobs, int64_t carry, int64_t pr
 
 // ---- launches --------------------------------------------------------------
 
-// Size-only calls on matrices below this many cells finish inside the tile
-// launch (its last block runs the fix-up and writes the result): one launch
-// per call, where the separate fix-up launch would cost more than the work.
+// Calls on matrices below this many cells finish inside the tile launch (its
+// last block runs the fix-up and writes the result): one launch per call,
+// where separate fix-up launches would cost more than the work.  The dp
+// map's in-block fix-up is the sequential strip one, hence the lower limit.
 constexpr int64_t kFusedFinishCells = (int64_t)1 << 24;
+constexpr int64_t kFusedFinishCellsDp = (int64_t)1 << 20;
 
 template <int FMT, bool DPMAP>
 cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   const int64_t ntiles = tiles_of(j);
-  const int fuse = (!DPMAP && j.bits_scratch && ntiles > 0 && j.m * j.n < kFusedFinishCells) ? 1 : 0;
+  const int fuse = ntiles > 0 && ((!DPMAP && j.bits_scratch && j.m * j.n < kFusedFinishCells) ||
+                                   (DPMAP && !j.test_hold && j.m * j.n < kFusedFinishCellsDp))
+                       ? 1 : 0;
   if (ntiles > 0) {
     ProfScope ps(ctx, s, kProfTile);
     const int64_t warps = (ntiles + 1) / 2;
@@ -413,7 +421,8 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
       ms::k_fixup_bits_one<FMT><<<team, 1024, sm, s>>>(j, (int64_t)(sm / 4),
                                                        team > 1 ? ctx->d_sync1 : nullptr);
     } else {
-      if (DPMAP && j.bits_scratch && !j.test_hold) {
+      const bool levels = DPMAP && j.bits_scratch && !j.test_hold;
+      if (levels) {
         // dp map: bitplane levels in the box, then every box cell's dp from
         // them; the strip kernel below only finalises unless the levels did
         // not fit the scratch (or the strip test hook is on)
@@ -426,7 +435,7 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
       const size_t sm = ring_bytes(ms::kFixWarps * 32);
       if (allow_smem((const void*)ms::k_fixup_one<FMT, DPMAP>, sm) != cudaSuccess)
         return cudaGetLastError();
-      ms::k_fixup_one<FMT, DPMAP><<<1, ms::kFixWarps * 32, sm, s>>>(j);
+      ms::k_fixup_one<FMT, DPMAP><<<1, ms::kFixWarps * 32, sm, s>>>(j, levels ? 1 : 0);
     }
   }
   return cudaGetLastError();

@@ -1194,19 +1194,21 @@ __device__ __forceinline__ void finalize_job(const Job& j) {
 }
 
 template <int FMT, bool DPMAP>
-__device__ __forceinline__ void fixup_job(const Job& j) {
+__device__ __forceinline__ void fixup_job(const Job& j, bool after_levels = true) {
   __shared__ int32_t sbox[4];
   JobState* st = j.st;
   if (threadIdx.x == 0) {
-    sbox[0] = st->box[0];
-    sbox[1] = st->box[1];
-    sbox[2] = st->box[2];
-    sbox[3] = st->box[3];
+    const volatile int32_t* b = st->box;
+    sbox[0] = b[0];
+    sbox[1] = b[1];
+    sbox[2] = b[2];
+    sbox[3] = b[3];
   }
   __syncthreads();
   const int rlo = sbox[0], rhi = sbox[1], clo = sbox[2], chi = sbox[3];
-  // a dp map already completed from bitplane levels needs no strips
-  const bool done = DPMAP && j.bits_scratch &&
+  // a dp map already completed from bitplane levels (launched just before
+  // this kernel) needs no strips
+  const bool done = DPMAP && after_levels && j.bits_scratch &&
                     reinterpret_cast<const LevelTab*>(j.bits_scratch)->n > 0;
   if (rhi > rlo && chi > clo && !done) {
     const int64_t br0 = max(0, rlo - kHalo);
@@ -1216,7 +1218,8 @@ __device__ __forceinline__ void fixup_job(const Job& j) {
     const int nstrips = (int)((chi - bc0 + kFixW - 1) / kFixW);
     const int rows = (int)(rhi - br0);
     const int warp = threadIdx.x >> 5;
-    for (int s = warp; s < nstrips && s < j.strips_fix; s += kFixWarps) {
+    const int nwarps = (int)(blockDim.x >> 5);  // strips go round-robin to the warps
+    for (int s = warp; s < nstrips && s < j.strips_fix; s += nwarps) {
       Tile g;
       g.base = reinterpret_cast<const uint8_t*>(j.data);
       g.ld = j.ld;
@@ -1311,33 +1314,38 @@ __global__ void __launch_bounds__(kFixWarps * 32, 1) k_fixup(const Job* __restri
   fixup_job<FMT, DPMAP>(job);
 }
 
+// after_levels: the dp-map level kernels ran just before (their table says
+// whether they completed the map).
 template <int FMT, bool DPMAP>
-__global__ void __launch_bounds__(kFixWarps * 32, 1) k_fixup_one(const Job job) {
-  fixup_job<FMT, DPMAP>(job);
+__global__ void __launch_bounds__(kFixWarps * 32, 1) k_fixup_one(const Job job, int after_levels) {
+  fixup_job<FMT, DPMAP>(job, after_levels != 0);
 }
 
 // Every variant fits 128 registers without spills, so two 256-thread blocks
 // share an SM.  Single matrix: the job travels as a kernel parameter.
 //
-// fuse != 0 (size-only, small matrices): the last block to finish also
-// finishes the matrix -- the bitplane fix-up of its box, if any, from the
-// block's ring memory or the job's scratch, then the result -- so that one
-// launch does the whole call.
+// fuse != 0 (small matrices): the last block to finish also finishes the
+// matrix -- the fix-up of its box, if any (size-only: bitplane growth from the
+// block's ring memory or the job's scratch; dp map: the strip fix-up over the
+// block's warps), then the result -- so that one launch does the whole call.
 template <int P, int FMT, bool DPMAP>
 __global__ void __launch_bounds__(256, 2) k_tiles_one(const Job job, int64_t ntiles, int fuse) {
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   tile_pass_warp<P, FMT, DPMAP>(&job, 1, ntiles, w);
-  if constexpr (!DPMAP) {
-    if (fuse) {
-      __shared__ int s_last;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        __threadfence();  // this block's key and box updates before its ticket
-        s_last = atomicAdd(&job.st->done, 1) == (int)gridDim.x - 1;
-        if (s_last) __threadfence();
-      }
-      __syncthreads();
-      if (s_last) {
+  if (fuse) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // this block's key and box updates before its ticket
+      s_last = atomicAdd(&job.st->done, 1) == (int)gridDim.x - 1;
+      if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last) {
+      if constexpr (DPMAP) {
+        // the strip fix-up over this block's warps and rings, then the result
+        fixup_job<FMT, true>(job, false);
+      } else {
         extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
         fixup_bits_job<FMT>(job, reinterpret_cast<uint32_t*>(ms_dyn_smem),
                             (int64_t)(blockDim.x >> 5) * kRingWarpBytes / 4, 1, 0, nullptr);

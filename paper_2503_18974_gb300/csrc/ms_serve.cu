@@ -83,7 +83,8 @@ struct Request {
   ms_matrix dev;   // resident copy
   size_t off = 0, bytes = 0;
   double t_submit = 0, t_admit = 0, t_launch = 0, t_done = 0;
-  cudaEvent_t copied = nullptr;
+  cudaEvent_t copied = nullptr;      // owned: recorded after this request's copy round
+  cudaEvent_t round_done = nullptr;  // the copy round's event (owned by its last request)
   ms_result result{};
 };
 
@@ -95,6 +96,7 @@ struct Lane {  // one compute stream with its context and result buffers
   cudaEvent_t done = nullptr;
   std::vector<Request*> batch;
   bool busy = false;
+  bool failed = false;  // the batch could not be launched; results already set
 };
 
 }  // namespace
@@ -117,6 +119,7 @@ struct ms_server {
   int64_t outstanding = 0;        // submitted and not completed
   bool stop = false;
   ms_server_stats stats{};
+  double host_copy_s = 0, host_batch_s = 0;
   std::thread worker;
   std::condition_variable idle_cv;
 };
@@ -151,28 +154,38 @@ void finish_request(ms_server* s, Request* r, std::vector<ms_server_completion>&
   delete r;
 }
 
-// One scheduler round; returns true if it made progress.
+// One scheduler round; returns true if it made progress.  The lock guards the
+// queues and statistics only: copies and batch launches are issued without
+// it, so submissions never wait for the scheduler's CUDA calls.  Lanes,
+// their batches and the admitted queue are touched by the scheduler thread
+// alone.
 bool schedule_round(ms_server* s) {
   bool progress = false;
   std::vector<ms_server_completion> finished;
+  std::vector<Request*> newly;
+  double copy_s = 0, batch_s = 0;
+  // 1. completions
+  for (Lane& ln : s->lanes) {
+    if (!ln.busy || ln.failed) continue;
+    const cudaError_t q = cudaEventQuery(ln.done);
+    if (q == cudaErrorNotReady) continue;
+    const double t = now_s();
+    for (size_t k = 0; k < ln.batch.size(); ++k) {
+      Request* r = ln.batch[k];
+      r->result = q == cudaSuccess ? ln.h_res[k] : ms_result{0, -1, -1, (int32_t)MS_ERR_CUDA};
+      r->t_done = t;
+    }
+    if (q != cudaSuccess) cudaGetLastError();
+    progress = true;
+  }
   {
-    std::unique_lock<std::mutex> lk(s->mu);
-    // 1. completions
+    std::lock_guard<std::mutex> lk(s->mu);
     for (Lane& ln : s->lanes) {
-      if (!ln.busy) continue;
-      const cudaError_t q = cudaEventQuery(ln.done);
-      if (q == cudaErrorNotReady) continue;
-      const double t = now_s();
-      for (size_t k = 0; k < ln.batch.size(); ++k) {
-        Request* r = ln.batch[k];
-        r->result = q == cudaSuccess ? ln.h_res[k] : ms_result{0, -1, -1, (int32_t)MS_ERR_CUDA};
-        r->t_done = t;
-        finish_request(s, r, finished);
-      }
-      if (q != cudaSuccess) cudaGetLastError();
+      if (!ln.busy || ln.batch.empty() || ln.batch[0]->t_done == 0) continue;
+      for (Request* r : ln.batch) finish_request(s, r, finished);
       ln.batch.clear();
       ln.busy = false;
-      progress = true;
+      ln.failed = false;
     }
     // 2. admission in arrival order while the arena has room
     while (!s->pending.empty()) {
@@ -182,66 +195,99 @@ bool schedule_round(ms_server* s) {
       s->pending.pop_front();
       r->off = off;
       r->t_admit = now_s();
-      const ms_matrix& h = r->host;
-      const size_t elem = h.fmt == MS_U8 ? 1 : 4;
-      const int64_t row = h.fmt == MS_U8 ? h.n : (h.n + 31) / 32;
-      const size_t dld_bytes = ((size_t)row * elem + 15) & ~(size_t)15;
-      r->dev = h;
-      r->dev.data = s->d_arena + off;
-      r->dev.ld = (int64_t)(dld_bytes / elem);
-      if (h.m > 0 && row > 0)
-        cudaMemcpy2DAsync(s->d_arena + off, dld_bytes, h.data, (size_t)h.ld * elem,
-                          (size_t)row * elem, (size_t)h.m, cudaMemcpyHostToDevice,
-                          s->copy_stream);
-      r->copied = take_event(s);
-      if (r->copied) cudaEventRecord(r->copied, s->copy_stream);
-      s->admitted.push_back(r);
+      newly.push_back(r);
       s->stats.peak_bytes = std::max<int64_t>(s->stats.peak_bytes, (int64_t)s->arena->used());
-      progress = true;
-    }
-    // 3. continuous batching: each free lane takes the copied requests
-    for (Lane& ln : s->lanes) {
-      if (ln.busy || s->admitted.empty()) continue;
-      std::vector<ms_matrix> descs;
-      while (!s->admitted.empty() && (int)ln.batch.size() < s->cfg.max_batch) {
-        Request* r = s->admitted.front();
-        if (r->copied && cudaEventQuery(r->copied) == cudaErrorNotReady) break;
-        s->admitted.pop_front();
-        ln.batch.push_back(r);
-        descs.push_back(r->dev);
-      }
-      if (ln.batch.empty()) continue;
-      const double t = now_s();
-      for (Request* r : ln.batch) r->t_launch = t;
-      ms_status st = ms_batch(ln.ctx, descs.data(), (int32_t)descs.size(), ln.d_res,
-                              reinterpret_cast<ms_stream_t>(ln.stream));
-      if (st == MS_OK &&
-          cudaMemcpyAsync(ln.h_res, ln.d_res, descs.size() * sizeof(ms_result),
-                          cudaMemcpyDeviceToHost, ln.stream) != cudaSuccess)
-        st = MS_ERR_CUDA;
-      if (st == MS_OK && cudaEventRecord(ln.done, ln.stream) != cudaSuccess) st = MS_ERR_CUDA;
-      if (st != MS_OK) {
-        cudaGetLastError();
-        for (Request* r : ln.batch) {
-          r->result = ms_result{0, -1, -1, (int32_t)st};
-          r->t_done = now_s();
-          finish_request(s, r, finished);
-        }
-        ln.batch.clear();
-        continue;
-      }
-      ln.busy = true;
-      s->stats.batches++;
-      int inflight = 0;
-      for (const Lane& l2 : s->lanes) inflight += l2.busy ? 1 : 0;
-      s->stats.peak_inflight = std::max(s->stats.peak_inflight, inflight);
-      progress = true;
     }
     for (const ms_server_completion& c : finished) s->done.push_back(c);
     s->stats.completed += (int64_t)finished.size();
     s->outstanding -= (int64_t)finished.size();
   }
   if (!finished.empty()) s->idle_cv.notify_all();
+  // copies of the newly admitted requests: one contiguous copy when the host
+  // rows are already packed like the device rows, one event per round
+  if (!newly.empty()) {
+    const double t0 = now_s();
+    for (Request* r : newly) {
+      const ms_matrix& h = r->host;
+      const size_t elem = h.fmt == MS_U8 ? 1 : 4;
+      const int64_t row = h.fmt == MS_U8 ? h.n : (h.n + 31) / 32;
+      const size_t dld_bytes = ((size_t)row * elem + 15) & ~(size_t)15;
+      r->dev = h;
+      r->dev.data = s->d_arena + r->off;
+      r->dev.ld = (int64_t)(dld_bytes / elem);
+      if (h.m > 0 && row > 0) {
+        if ((size_t)h.ld * elem == dld_bytes)
+          cudaMemcpyAsync(s->d_arena + r->off, h.data, dld_bytes * (size_t)h.m,
+                          cudaMemcpyHostToDevice, s->copy_stream);
+        else
+          cudaMemcpy2DAsync(s->d_arena + r->off, dld_bytes, h.data, (size_t)h.ld * elem,
+                            (size_t)row * elem, (size_t)h.m, cudaMemcpyHostToDevice,
+                            s->copy_stream);
+      }
+    }
+    cudaEvent_t e = take_event(s);
+    if (e) cudaEventRecord(e, s->copy_stream);
+    for (size_t k = 0; k < newly.size(); ++k) {
+      newly[k]->copied = (k + 1 == newly.size()) ? e : nullptr;  // the round's last owns it
+      newly[k]->round_done = e;
+      s->admitted.push_back(newly[k]);
+    }
+    copy_s += now_s() - t0;
+    progress = true;
+  }
+  // 3. continuous batching: each free lane takes the copied requests
+  for (Lane& ln : s->lanes) {
+    if (ln.busy || s->admitted.empty()) continue;
+    const double t0 = now_s();
+    std::vector<ms_matrix> descs;
+    cudaEvent_t last_ok = nullptr;
+    while (!s->admitted.empty() && (int)ln.batch.size() < s->cfg.max_batch) {
+      Request* r = s->admitted.front();
+      if (r->round_done && r->round_done != last_ok) {
+        if (cudaEventQuery(r->round_done) == cudaErrorNotReady) break;
+        last_ok = r->round_done;
+      }
+      s->admitted.pop_front();
+      ln.batch.push_back(r);
+      descs.push_back(r->dev);
+    }
+    if (ln.batch.empty()) continue;
+    const double t = now_s();
+    for (Request* r : ln.batch) {
+      r->t_launch = t;
+      r->t_done = 0;
+    }
+    ms_status st = ms_batch(ln.ctx, descs.data(), (int32_t)descs.size(), ln.d_res,
+                            reinterpret_cast<ms_stream_t>(ln.stream));
+    if (st == MS_OK &&
+        cudaMemcpyAsync(ln.h_res, ln.d_res, descs.size() * sizeof(ms_result),
+                        cudaMemcpyDeviceToHost, ln.stream) != cudaSuccess)
+      st = MS_ERR_CUDA;
+    if (st == MS_OK && cudaEventRecord(ln.done, ln.stream) != cudaSuccess) st = MS_ERR_CUDA;
+    if (st != MS_OK) {
+      cudaGetLastError();
+      for (Request* r : ln.batch) {
+        r->result = ms_result{0, -1, -1, (int32_t)st};
+        r->t_done = now_s();
+      }
+      ln.failed = true;
+    }
+    ln.busy = true;  // a failed batch completes at the next round
+    int inflight = 0;
+    for (const Lane& l2 : s->lanes) inflight += l2.busy ? 1 : 0;
+    batch_s += now_s() - t0;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (st == MS_OK) s->stats.batches++;
+      s->stats.peak_inflight = std::max(s->stats.peak_inflight, inflight);
+    }
+    progress = true;
+  }
+  if (copy_s > 0 || batch_s > 0) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->host_copy_s += copy_s;
+    s->host_batch_s += batch_s;
+  }
   return progress;
 }
 
@@ -361,6 +407,8 @@ ms_status ms_server_stats_get(ms_server* s, ms_server_stats* out) {
   if (!s || !out) return MS_ERR_INVALID;
   std::lock_guard<std::mutex> lk(s->mu);
   *out = s->stats;
+  out->host_batch_s = s->host_batch_s;
+  out->host_copy_s = s->host_copy_s;
   return MS_OK;
 }
 
