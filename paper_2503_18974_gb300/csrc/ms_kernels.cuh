@@ -96,11 +96,28 @@ constexpr int kRingWarpBytes = 8192;
 
 template <int P, int FMT>
 struct RingGeom {
-  static constexpr int kLane = (FMT == MS_U8 && P > 16) ? 32 : 16;  // bytes per lane and tile
+  // bytes per lane and tile in a slot (16, or 32 for 32-byte chunks; deeper
+  // rings for narrow chunks measured no faster)
+  static constexpr int kLane = (FMT == MS_U8 && P > 16) ? 32 : 16;
   static constexpr int kSlot = 2 * 32 * kLane;
   static constexpr int kDepth = kRingWarpBytes / kSlot;
   static_assert((kDepth & (kDepth - 1)) == 0 && kDepth >= 2, "ring depth: a power of two");
 };
+
+// Zero (or write w[]) the kLane bytes at shared address a.
+template <int kLane>
+__device__ __forceinline__ void st_shared_chunk(uint32_t a, const uint32_t* w) {
+  if constexpr (kLane == 4) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(w[0]) : "memory");
+  } else if constexpr (kLane == 8) {
+    asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(w[0]), "r"(w[1]) : "memory");
+  } else {
+#pragma unroll
+    for (int h = 0; h < kLane / 4; h += 4)
+      asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a + 4 * h), "r"(w[h]),
+                   "r"(w[h + 1]), "r"(w[h + 2]), "r"(w[h + 3]) : "memory");
+  }
+}
 
 __device__ __forceinline__ void cp_async(uint32_t dst, const void* src, int bytes_copy,
                                          int bytes_src) {
@@ -134,6 +151,7 @@ struct AsyncReader {
   int mode;             // 0: no cells (slots stay zero), 1: async copy, 2: synchronous
   int nvalid;
   uint32_t dst;         // this lane's place in slot 0
+  uint32_t lshift;      // chunks under 4 bytes: bit offset of the chunk in its copied word
 
   __device__ __forceinline__ void init(const Tile& g, int lane, int first_row, uint32_t ring,
                                        int half) {
@@ -142,12 +160,24 @@ struct AsyncReader {
     nrows = g.nrows;
     dst = ring + half * (32 * G::kLane) + lane * G::kLane;
     safe = g.base;
+    lshift = 0;
     if constexpr (FMT == MS_U8) {
       stride = g.ld;
-      ptr = g.base + (g.wr0 + first_row) * g.ld + col;
       const int64_t valid = g.n - col;
       nvalid = (int)(valid < P ? (valid < 0 ? 0 : valid) : P);
-      mode = nvalid == 0 ? 0 : ((nvalid == P && g.aligned && P >= 4) ? 1 : 2);
+      if constexpr (P >= 4) {
+        ptr = g.base + (g.wr0 + first_row) * g.ld + col;
+        mode = nvalid == 0 ? 0 : ((nvalid == P && g.aligned) ? 1 : 2);
+      } else {
+        // 1- and 2-byte chunks are fetched as the aligned 4-byte word holding
+        // them (asynchronously, like the wider chunks), unless that word
+        // reaches past the row's last column
+        const int64_t col4 = col & ~(int64_t)3;
+        const bool word_ok = g.aligned && col4 + 4 <= g.n;
+        ptr = g.base + (g.wr0 + first_row) * g.ld + (word_ok ? col4 : col);
+        lshift = word_ok ? (uint32_t)(8 * (col - col4)) : 0u;
+        mode = nvalid == 0 ? 0 : ((nvalid == P && word_ok) ? 1 : 2);
+      }
     } else {
       stride = g.ld * 4;
       ptr = g.base + ((g.wr0 + first_row) * g.ld + (col >> 5)) * 4;
@@ -155,12 +185,11 @@ struct AsyncReader {
       mode = col < g.n ? 1 : 0;
     }
     // slots start as zeros: mode 0 never writes, the others overwrite
+    uint32_t zero[G::kLane / 4];
 #pragma unroll
-    for (int k = 0; k < G::kDepth; ++k)
+    for (int b = 0; b < G::kLane / 4; ++b) zero[b] = 0u;
 #pragma unroll
-      for (int h = 0; h < G::kLane; h += 16)
-        asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst + k * G::kSlot + h),
-                     "r"(0u) : "memory");
+    for (int k = 0; k < G::kDepth; ++k) st_shared_chunk<G::kLane>(dst + k * G::kSlot, zero);
   }
 
   // copy window row `row` into `slot` and advance
@@ -172,6 +201,8 @@ struct AsyncReader {
       if constexpr (kBytes > 16) {
         cp_async(d, src, 16, ok ? 16 : 0);
         cp_async(d + 16, src + 16, 16, ok ? 16 : 0);
+      } else if constexpr (kBytes < 4) {
+        cp_async(d, src, 4, ok ? 4 : 0);
       } else {
         cp_async(d, src, kBytes, ok ? kBytes : 0);
       }
@@ -182,10 +213,7 @@ struct AsyncReader {
       for (int b = 0; b < NW; ++b) w[b] = 0u;
       if (ok)
         for (int b = 0; b < nvalid; ++b) w[b >> 2] |= (uint32_t)__ldg(ptr + b) << (8 * (b & 3));
-#pragma unroll
-      for (int h = 0; h < NW; h += 4)
-        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(d + 4 * h), "r"(w[h]),
-                     "r"(w[h + 1]), "r"(w[h + 2]), "r"(w[h + 3]) : "memory");
+      st_shared_chunk<G::kLane>(d, w);
     }
     ptr += stride;
     ++row;
@@ -210,6 +238,7 @@ struct AsyncReader {
                      : "memory");
       } else {
         asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r.w[0]) : "r"(a) : "memory");
+        if constexpr (P < 4) r.w[0] >>= lshift;
       }
     } else {
       asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r.word) : "r"(a) : "memory");
