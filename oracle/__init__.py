@@ -30,6 +30,11 @@ class _Result(ctypes.Structure):
                 ("status", ctypes.c_int32)]
 
 
+class _Cube(ctypes.Structure):
+    _fields_ = [("side", ctypes.c_int32), ("slice", ctypes.c_int32), ("row", ctypes.c_int32),
+                ("col", ctypes.c_int32)]
+
+
 def build(force: bool = False) -> str:
     srcs = [os.path.join(_HERE, f) for f in ("oracle.c", "oracle.h")]
     if force or not os.path.exists(_SO) or any(os.path.getmtime(s) > os.path.getmtime(_SO)
@@ -56,6 +61,8 @@ def _l():
         lib.oracle_all_max.restype = ctypes.c_int
         lib.oracle_all_max.argtypes = [_vp, _i64, _i64, _i64, _vp, _i64,
                                        ctypes.POINTER(_i64), ctypes.POINTER(_Result)]
+        lib.oracle_cube.restype = ctypes.c_int
+        lib.oracle_cube.argtypes = [_vp, _i64, _i64, _i64, _i64, _i64, ctypes.POINTER(_Cube)]
         lib.oracle_erode.restype = ctypes.c_int
         lib.oracle_erode.argtypes = [_vp, _i64, _i64, _i64, _i64, _vp, _i64]
         _lib = lib
@@ -145,6 +152,20 @@ def all_max(a: np.ndarray, n: int | None = None):
         _check(_l().oracle_all_max(a.ctypes.data, m, n, ld, out.ctypes.data, cnt.value,
                                    ctypes.byref(cnt), ctypes.byref(res)), "oracle_all_max")
     return _tuple(res), out[:cnt.value]
+
+
+def cube(v: np.ndarray):
+    """Largest all-ones cube of a (d, m, n) volume: (side, slice, row, col) of
+    the first corner, in (z, i, j) order, of a largest cube."""
+    v = np.ascontiguousarray(np.asarray(v), dtype=np.uint8)
+    if v.ndim != 3:
+        raise ValueError("expected a 3-D volume")
+    d, m, n = v.shape
+    res = _Cube()
+    buf = v if v.size else np.zeros(1, dtype=np.uint8)
+    _check(_l().oracle_cube(buf.ctypes.data, d, m, n, max(n, 1), max(m * n, 1),
+                            ctypes.byref(res)), "oracle_cube")
+    return (int(res.side), int(res.slice), int(res.row), int(res.col))
 
 
 def erode(a: np.ndarray, t: int, n: int | None = None) -> np.ndarray:

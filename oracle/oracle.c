@@ -258,3 +258,47 @@ int oracle_all_max(const uint8_t* v, int64_t m, int64_t n, int64_t ld, int32_t* 
   free(cur);
   return 0;
 }
+
+/* Two slices of c are kept: prev = slice z-1, cur = slice z (m x n each). */
+int oracle_cube(const uint8_t* v, int64_t d, int64_t m, int64_t n, int64_t ld, int64_t ld_slice,
+                oracle_cube_result* out) {
+  out->side = 0;
+  out->slice = out->row = out->col = -1;
+  if (d <= 0 || m <= 0 || n <= 0) return 0;
+  int32_t* prev = (int32_t*)calloc((size_t)(m * n), sizeof(int32_t));
+  int32_t* cur = (int32_t*)calloc((size_t)(m * n), sizeof(int32_t));
+  if (!prev || !cur) {
+    free(prev);
+    free(cur);
+    return -1;
+  }
+#define C(t, i, j) (((i) < 0 || (j) < 0) ? 0 : (t)[(i) * n + (j)])
+  for (int64_t z = 0; z < d; ++z) {
+    for (int64_t i = 0; i < m; ++i) {
+      for (int64_t j = 0; j < n; ++j) {
+        int32_t c = 0;
+        if (v[z * ld_slice + i * ld + j] != 0) {
+          int32_t mn = C(prev, i, j);
+          const int32_t nb[6] = {C(prev, i - 1, j), C(prev, i, j - 1), C(prev, i - 1, j - 1),
+                                 C(cur, i - 1, j), C(cur, i, j - 1), C(cur, i - 1, j - 1)};
+          for (int k = 0; k < 6; ++k) mn = nb[k] < mn ? nb[k] : mn;
+          c = mn + 1;
+        }
+        cur[i * n + j] = c;
+        if (c > out->side) {
+          out->side = c;
+          out->slice = (int32_t)z;
+          out->row = (int32_t)i;
+          out->col = (int32_t)j;
+        }
+      }
+    }
+    int32_t* t = prev;
+    prev = cur;
+    cur = t;
+  }
+#undef C
+  free(prev);
+  free(cur);
+  return 0;
+}

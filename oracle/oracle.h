@@ -26,6 +26,7 @@
  *   oracle_brute       pinned: independent numpy enumeration, closed forms
  *   oracle_erode       pinned: equals [dp >= t], closed forms
  *   oracle_all_max     pinned: brute-force enumeration, closed forms
+ *   oracle_cube        pinned: brute-force enumeration, closed forms, slices
  */
 #ifndef MS_ORACLE_H
 #define MS_ORACLE_H
@@ -75,6 +76,18 @@ int oracle_erode(const uint8_t* v, int64_t m, int64_t n, int64_t ld, int64_t t, 
  * *count (none when K == 0).  Returns 0, or -1 on allocation failure. */
 int oracle_all_max(const uint8_t* v, int64_t m, int64_t n, int64_t ld, int32_t* corners,
                    int64_t cap, int64_t* count, oracle_result* out);
+
+/* Largest all-ones cube of a 3-D volume (the paper's future-work extension,
+ * Sec. 6): v[z*ld_slice + i*ld + j] for z < d, i < m, j < n.  The 3-D
+ * analogue of Eq. 1: c[z][i][j] = 1 + min of the seven neighbours that
+ * precede it in z, i or j (0 outside the volume) on a one, 0 on a zero.
+ * side = max c; (slice, row, col) = the first corner in (z, i, j) order with
+ * c == side, or -1s when side == 0.  Returns 0, or -1 on allocation failure. */
+typedef struct {
+  int32_t side, slice, row, col;
+} oracle_cube_result;
+int oracle_cube(const uint8_t* v, int64_t d, int64_t m, int64_t n, int64_t ld, int64_t ld_slice,
+                oracle_cube_result* out);
 
 #ifdef __cplusplus
 }

@@ -365,3 +365,60 @@ def test_all_max_closed_forms():
     (K, r, c), corners = oracle.all_max(a)
     assert K == 8 and [tuple(p) for p in corners.tolist()] == [(10, 12), (27, 37)]
     assert (r, c) == (10, 12)
+
+
+# ------------------------------------------------------------- 3-D cubes ----
+
+def np_cube(v):
+    """Independent enumeration: 3-D prefix sums; the t-cube ending at
+    (z, i, j) is all ones iff its sum is t^3; the first corner in (z, i, j)
+    order at the largest t."""
+    x = (np.asarray(v) != 0).astype(np.int64)
+    d, m, n = x.shape
+    if x.size == 0:
+        return (0, -1, -1, -1)
+    S = np.zeros((d + 1, m + 1, n + 1), dtype=np.int64)
+    S[1:, 1:, 1:] = x.cumsum(0).cumsum(1).cumsum(2)
+    best = (0, -1, -1, -1)
+    for t in range(1, min(d, m, n) + 1):
+        w = (S[t:, t:, t:] - S[:-t, t:, t:] - S[t:, :-t, t:] - S[t:, t:, :-t]
+             + S[:-t, :-t, t:] + S[:-t, t:, :-t] + S[t:, :-t, :-t] - S[:-t, :-t, :-t])
+        hit = np.argwhere(w == t ** 3)
+        if len(hit) == 0:
+            break
+        z, i, j = hit[0]  # argwhere is in (z, i, j) lexicographic order
+        best = (t, int(z) + t - 1, int(i) + t - 1, int(j) + t - 1)
+    return best
+
+
+def test_cube_against_enumeration():
+    rng = np.random.default_rng(2025)
+    for trial in range(300):
+        d, m, n = (int(rng.integers(1, 8)) for _ in range(3))
+        v = (rng.random((d, m, n)) < rng.uniform(0.5, 0.97)).astype(np.uint8)
+        assert oracle.cube(v) == np_cube(v), (d, m, n)
+    # every 2 x 2 x 2 volume
+    for bits in range(256):
+        v = np.array([(bits >> k) & 1 for k in range(8)], dtype=np.uint8).reshape(2, 2, 2)
+        assert oracle.cube(v) == np_cube(v)
+
+
+def test_cube_closed_forms_and_slices():
+    for d, m, n in [(1, 1, 1), (3, 5, 7), (6, 4, 9), (8, 8, 8)]:
+        s = min(d, m, n)
+        assert oracle.cube(np.ones((d, m, n), dtype=np.uint8)) == (s, s - 1, s - 1, s - 1)
+        assert oracle.cube(np.zeros((d, m, n), dtype=np.uint8)) == (0, -1, -1, -1)
+    assert oracle.cube(np.zeros((0, 3, 3), dtype=np.uint8)) == (0, -1, -1, -1)
+    # one slice: a cube of side 1 at most, the first one in the slice
+    rng = np.random.default_rng(4)
+    a = (rng.random((20, 30)) < 0.6).astype(np.uint8)
+    first = np.argwhere(a)[0]
+    assert oracle.cube(a[None]) == (1, 0, int(first[0]), int(first[1]))
+    # a planted cube in a sparse volume, and a stack of planted squares of
+    # side s over s slices is a cube
+    v = np.zeros((12, 15, 16), dtype=np.uint8)
+    v[2:7, 4:9, 3:8] = 1
+    assert oracle.cube(v) == (5, 6, 8, 7)
+    v2 = (rng.random((10, 40, 40)) < 0.3).astype(np.uint8)
+    v2[1:7, 10:16, 20:26] = 1
+    assert oracle.cube(v2)[0] == 6
