@@ -143,6 +143,35 @@ ms_status ms_destroy(ms_ctx* ctx);
  *   them on one stream or synchronise between them. */
 ms_status ms_max_square_noalloc(const ms_matrix* in, ms_result* out_dev, ms_stream_t s);
 
+/* ---- 3-D volumes (the paper's future-work extension, Sec. 6) ---------------
+ * A uint8 volume in device memory: cell (z, i, j) at
+ * data[z*ld_slice + i*ld + j] for z < d, i < m, j < n; nonzero = 1. */
+typedef struct {
+  const void* data;
+  int64_t d, m, n;
+  int64_t ld;        /* bytes between rows, >= n */
+  int64_t ld_slice;  /* bytes between slices, >= (m-1)*ld + n */
+  int32_t fmt;       /* MS_U8 */
+  int32_t reserved;  /* 0 */
+} ms_volume;
+
+typedef struct {
+  int32_t side;               /* largest all-ones cube */
+  int32_t slice, row, col;    /* its first corner in (z, i, j) order, -1s if side == 0 */
+  int32_t status;
+  int32_t reserved;
+} ms_cube_result;
+
+/* Largest all-ones cube of a volume and the first corner (in (z, i, j)
+ * order) of such a cube: the 3-D analogue of Eq. 1, computed by bitplane
+ * growth (cube corners of side a + s from those of side a, 0 < s <= a).
+ * `out_dev` is one ms_cube_result in device memory.  The call decides each
+ * growth step from the previous one and so waits for the stream between
+ * steps (it returns after the result is written).  Scratch (two bit volumes,
+ * d*m*ceil(n/32) words each) is allocated stream-ordered for the call.
+ * Limits: d, m, n < 2^31 and d*m*n < 2^62. */
+ms_status ms_max_cube(ms_ctx* ctx, const ms_volume* in, ms_cube_result* out_dev, ms_stream_t s);
+
 /* Static, human-readable name of a status code. */
 const char* ms_status_string(ms_status st);
 

@@ -20,9 +20,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libms.so")
 _SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu", "ms_serve.cu",
-                                                      "ms_kernels.cuh", "ms_device.cuh",
-                                                      "ms_bits.cuh")]
-_UNITS = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu", "ms_serve.cu")]
+                                                      "ms_cube.cu", "ms_kernels.cuh",
+                                                      "ms_device.cuh", "ms_bits.cuh")]
+_UNITS = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu", "ms_serve.cu",
+                                                    "ms_cube.cu")]
 _HEADER = os.path.join(_ROOT, "include", "ms.h")
 
 MS_U8 = 0
@@ -31,7 +32,7 @@ STATUS = {0: "MS_OK", 1: "MS_ERR_INVALID", 2: "MS_ERR_OOM", 3: "MS_ERR_CUDA",
           4: "MS_ERR_TIMEOUT", 5: "MS_ERR_BUDGET", 6: "MS_ERR_UNSUPPORTED"}
 
 NVCC_FLAGS = ["-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-              "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo"]
+              "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "--threads", "4"]
 
 
 class MSError(RuntimeError):
@@ -51,6 +52,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd.insert(1, "-Xptxas=-v")
         subprocess.check_call(cmd)
     return LIB_PATH
+
+
+class _Volume(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("d", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("n", ctypes.c_int64), ("ld", ctypes.c_int64), ("ld_slice", ctypes.c_int64),
+                ("fmt", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class _Matrix(ctypes.Structure):
@@ -97,7 +104,7 @@ class ServerStats(ctypes.Structure):
 _lib = None
 
 EXPORTS = ("ms_create", "ms_destroy", "ms_max_square", "ms_dp_map", "ms_all_max_squares",
-           "ms_batch",
+           "ms_max_cube", "ms_batch",
            "ms_status_string", "ms_set_tuning", "ms_get_tuning", "ms_profile_start",
            "ms_profile_stop", "ms_autotune", "ms_max_square_noalloc", "ms_server_create",
            "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats_get",
@@ -120,6 +127,8 @@ def lib():
         L.ms_max_square.argtypes = [vp, ctypes.POINTER(_Matrix), vp, vp]
         L.ms_dp_map.restype = ctypes.c_int
         L.ms_dp_map.argtypes = [vp, ctypes.POINTER(_Matrix), vp, i64, vp, vp]
+        L.ms_max_cube.restype = ctypes.c_int
+        L.ms_max_cube.argtypes = [vp, ctypes.POINTER(_Volume), vp, vp]
         L.ms_all_max_squares.restype = ctypes.c_int
         L.ms_all_max_squares.argtypes = [vp, ctypes.POINTER(_Matrix), vp, i64, vp, vp, vp]
         L.ms_batch.restype = ctypes.c_int
@@ -252,6 +261,23 @@ class MaxSquare:
             out = torch.empty(4, dtype=torch.int32, device=x.device)
         _check(lib().ms_max_square(self._h, ctypes.byref(desc), out.data_ptr(),
                                    _stream_ptr(stream)), "ms_max_square")
+        return out
+
+    def max_cube(self, v, stream=None):
+        """Largest all-ones cube of a (d, m, n) uint8 CUDA tensor with unit
+        column stride.  Returns an int32 tensor [side, slice, row, col,
+        status, 0] (the call waits for the stream)."""
+        import torch
+        if v.dim() != 3 or v.dtype != torch.uint8 or (v.numel() and v.stride(2) != 1):
+            raise ValueError("expected a 3-D uint8 tensor with unit column stride")
+        d, m, n = v.shape
+        desc = _Volume(v.data_ptr() if v.numel() else None, d, m, n,
+                       v.stride(1) if m > 1 else max(n, 1),
+                       v.stride(0) if d > 1 else max(m * (v.stride(1) if m > 1 else n), 1),
+                       MS_U8, 0)
+        out = torch.empty(6, dtype=torch.int32, device=v.device)
+        _check(lib().ms_max_cube(self._h, ctypes.byref(desc), out.data_ptr(),
+                                 _stream_ptr(stream)), "ms_max_cube")
         return out
 
     def all_max_squares(self, x, n: int | None = None, fmt: int | None = None,

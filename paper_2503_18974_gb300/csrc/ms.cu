@@ -772,6 +772,12 @@ ms_status ms_dp_map(ms_ctx* ctx, const ms_matrix* in, int32_t* dp_dev, int64_t l
   return run_single(ctx, in, dp_dev, ld_dp, out_dev, reinterpret_cast<cudaStream_t>(s));
 }
 
+// Device of a context (for the 3-D path in its own translation unit; not
+// exported from the library).
+__attribute__((visibility("hidden"))) int ms_ctx_device(const ms_ctx* ctx) {
+  return ctx->device;
+}
+
 extern "C" ms_status ms_all_max_squares(ms_ctx* ctx, const ms_matrix* in, int32_t* corners_dev,
                                         int64_t capacity, int64_t* count_dev,
                                         ms_result* out_dev, ms_stream_t s) {

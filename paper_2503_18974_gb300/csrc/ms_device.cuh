@@ -178,6 +178,19 @@ struct Cells<P, MS_BITS32> {
   uint32_t bits;
 };
 
+// Bytes known to be 0 or 1 need no nonzero test: a shift puts each byte's
+// bit 0 into its most significant bit.  Every raw word is ORed into `seen`,
+// so the caller can tell afterwards whether the assumption held.
+template <int P>
+__device__ __forceinline__ Cells<P, MS_U8> cells_of01(const Raw<P, MS_U8>& r, uint32_t& seen) {
+  Cells<P, MS_U8> c;
+#pragma unroll
+  for (int i = 0; i < Raw<P, MS_U8>::W; ++i) {
+    c.w[i] = r.w[i] << 7;
+    seen |= r.w[i];
+  }
+  return c;
+}
 template <int P>
 __device__ __forceinline__ Cells<P, MS_U8> cells_of(const Raw<P, MS_U8>& r, const LaneCols&) {
   Cells<P, MS_U8> c;

@@ -301,12 +301,18 @@ __device__ __forceinline__ void store_dp(int32_t* p, const uint32_t* Ap, uint32_
 //
 // EMIT (second pass of the all-largest-squares call, largest side emitK <=
 // kHalo known): every counted cell with dp == emitK is appended to ej's list.
-template <int P, int FMT, bool DPMAP, int MODE, bool EMIT = false>
-__device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_t* dpa,
+//
+// B01 (uint8 tile pass): the bytes are taken to be 0 or 1 (cheaper cell
+// extraction); returns false if some byte of the tiles was larger, in which
+// case the caller computes the tiles again without the assumption.
+template <int P, int FMT, bool DPMAP, int MODE, bool EMIT = false, bool B01 = false>
+__device__ __forceinline__ bool run_tiles(const Tile& ta, const Tile& tb, int32_t* dpa,
                                           int64_t lda, int dpa_al, int32_t* dpb, int64_t ldb,
                                           int dpb_al, const StripIO& io, Best& ba, Best& bb,
                                           uint32_t ring, const Job* ej = nullptr,
                                           uint32_t emitK = 0) {
+  static_assert(!B01 || FMT == MS_U8, "the 0/1 shortcut is for bytes");
+  uint32_t seen = 0;  // B01: OR of every raw input word
   const int lane = threadIdx.x & 31;
   constexpr uint32_t kB2 = kBias * 0x10001u;
   constexpr int D = RingGeom<P, FMT>::kDepth;  // rows of input in flight per lane
@@ -366,8 +372,14 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
       Raw<P, FMT> rlo, rhi;
       rda.read(d, rlo);
       rdb.read(d, rhi);
-      const Cells<P, FMT> clo = cells_of<P>(rlo, lca);
-      const Cells<P, FMT> chi = cells_of<P>(rhi, lcb);
+      Cells<P, FMT> clo, chi;
+      if constexpr (B01) {
+        clo = cells_of01<P>(rlo, seen);
+        chi = cells_of01<P>(rhi, seen);
+      } else {
+        clo = cells_of<P>(rlo, lca);
+        chi = cells_of<P>(rhi, lcb);
+      }
       if ((unsigned)ir < (unsigned)nmax) {
         const uint32_t I = (uint32_t)ir + 1u + kBias;
         const uint32_t I2 = I * 0x10001u;
@@ -511,6 +523,8 @@ __device__ __forceinline__ void run_tiles(const Tile& ta, const Tile& tb, int32_
     }
   }
   cp_async_wait<0>();
+  if constexpr (B01) return __any_sync(kFull, (seen & 0xfefefefeu) != 0u) == 0;
+  return true;
 }
 
 // Reduce a per-lane best to the tile's key; returns the tile's largest value.
@@ -536,8 +550,14 @@ __device__ __forceinline__ void tile_pair(const Job& A, const Tile& ga, const Jo
                                           const Tile& gb, bool has_b) {
   StripIO io{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
   Best ba, bb;
-  run_tiles<P, FMT, DPMAP, 0>(ga, gb, A.dp, A.ld_dp, A.dp_aligned, B.dp, B.ld_dp, B.dp_aligned,
-                              io, ba, bb, warp_ring());
+  bool done = false;
+  if constexpr (FMT == MS_U8)  // most inputs hold only 0/1 bytes
+    done = run_tiles<P, FMT, DPMAP, 0, false, true>(ga, gb, A.dp, A.ld_dp, A.dp_aligned, B.dp,
+                                                    B.ld_dp, B.dp_aligned, io, ba, bb,
+                                                    warp_ring());
+  if (!done)
+    run_tiles<P, FMT, DPMAP, 0>(ga, gb, A.dp, A.ld_dp, A.dp_aligned, B.dp, B.ld_dp, B.dp_aligned,
+                                io, ba, bb, warp_ring());
   const unsigned long long ka = tile_key(ba, ga.n);
   const unsigned long long kb = tile_key(bb, gb.n);
   // the tile's cells above the halo: bounding box over the warp's lanes
