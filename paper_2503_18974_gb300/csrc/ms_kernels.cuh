@@ -1353,16 +1353,6 @@ static __global__ void __launch_bounds__(kBitsMixedThreads, 2)
     fixup_bits_job<MS_BITS32>(job, smem, smem_words, t.size, t.rank, syncs + t.job);
 }
 
-template <int FMT, bool DPMAP>
-__global__ void __launch_bounds__(kFixWarps * 32, 1) k_fixup(const Job* __restrict__ jobs,
-                                                          int njobs) {
-  const int j = blockIdx.x;
-  if (j >= njobs) return;
-  const Job job = jobs[j];
-  if (job.fmt != FMT) return;
-  fixup_job<FMT, DPMAP>(job);
-}
-
 // after_levels: the dp-map level kernels ran just before (their table says
 // whether they completed the map).
 template <int FMT, bool DPMAP>
