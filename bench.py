@@ -468,9 +468,9 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.set_device(device)
     ms.build()
     ctx = ms.MaxSquare(local)
-    packed_path = args.packed_path
-    if packed_path is None:
-        packed_path = 1 if ("bits" in args.workload and not args.workload.endswith("-dp")) else 0
+    # packed size-only work: the autotuner below chooses between the tile
+    # kernel and the bitplane search unless --packed-path fixes it
+    packed_path = args.packed_path if args.packed_path is not None else 0
     ctx.set_tuning(packed_path=packed_path, band_rows=args.band_rows, lane_cols=args.lane_cols)
     wl = make_workload(args.workload, device, host=True)
     torch.cuda.synchronize()
@@ -483,7 +483,7 @@ def run_ours(args, world, rank, local, pg):
     # the plain form: one autotune per workload class (format, log2 cells) on
     # a representative matrix, cached in the context for the plain calls
     plain_tuned = {}
-    if not wl.dpmap and not args.band_rows and not args.lane_cols and packed_path == 0:
+    if not wl.dpmap and not args.band_rows and not args.lane_cols and args.packed_path is None:
         classes = {}
         for mt in wl.mats:
             classes.setdefault((mt.fmt, int(math.log2(max(mt.m * mt.n, 1)))), []).append(mt)
@@ -788,7 +788,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--requests", type=int, default=20000)
     ap.add_argument("--packed-path", type=int, default=None,
-                    help="1: bitplane search for packed size-only work (default for c3-bits)")
+                    help="packed size-only work: 0 tile kernel, 1 bitplane search "
+                         "(default: the autotuner's choice)")
     ap.add_argument("--band-rows", type=int, default=0,
                     help="rows per tile (0: automatic, or autotuned for multi-matrix runs)")
     ap.add_argument("--lane-cols", type=int, default=0,
