@@ -730,13 +730,15 @@ struct Team {
 
 // Visits the cells (r, c) of a rows x cols grid, spread over the team's
 // threads in row-major order; the row/column step is kept incrementally.
-template <class F>
+// U cells per thread are unrolled (more for passes whose loads come from
+// global memory, so that their latencies overlap).
+template <int U = 2, class F>
 __device__ __forceinline__ void for_cells(const Team& tm, int rows, int cols, F&& f) {
   if (rows <= 0 || cols <= 0) return;
   const int bd = tm.threads(), t0 = tm.thread();
   const int dr = bd / cols, dc = bd - dr * cols;
   int r = t0 / cols, c = t0 - r * cols;
-#pragma unroll 2
+#pragma unroll U
   for (; r < rows;) {
     f(r, c);
     r += dr;
@@ -918,7 +920,7 @@ __device__ __forceinline__ Plane build_s32(const Job& j, const BitGeo& g, uint32
   const int RP = g.RP, Wv = g.Wv, R1 = g.R1, W1 = g.W1, ra = g.ra, wa = g.wa, pa = g.pa;
   Team& tm = *pb.tm;
   // 1. input bits of rows [pa, rhi), words [wa-1, whi)
-  for_cells(tm, RP, Wv, [&](int rr, int cc) {
+  for_cells<8>(tm, RP, Wv, [&](int rr, int cc) {
     in[rr * Wv + cc] = input_word<FMT>(j, pa + rr, wa - 1 + cc);
   });
   tm.barrier();
