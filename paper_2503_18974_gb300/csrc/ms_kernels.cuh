@@ -856,17 +856,27 @@ __device__ __forceinline__ void grow_pass(const Plane& L, Plane& O, int o_r1, in
   int rmin = 0x7fffffff, rmax = -1, wmin = 0x7fffffff, wmax = -1;
   unsigned long long f = ~0ull;
   pb.begin();
+  // (i, w) runs over L's active box, so only the shifted reads (rows i - d,
+  // words w - q and w - q - 1) can fall outside it; the matrix's last word
+  // is the only partial one
+  const int wlast = (int)((n - 1) >> 5);
+  const uint32_t lastmask = (n & 31) ? ((1u << (n & 31)) - 1u) : 0xffffffffu;
   for_cells(*pb.tm, r1 - r0, w1 - w0, [&](int rr, int cc) {
     const int i = r0 + rr, w = w0 + cc;
-    const uint32_t a0 = L.get(i, w), a1 = L.get(i - d, w);
-    uint32_t a2 = L.get(i, w - q), a3 = L.get(i - d, w - q);
+    const uint32_t* row = L.p + (i - L.r0) * L.pitch - L.w0;
+    const bool up_ok = i - d >= L.ar0;
+    const uint32_t* up = row - d * L.pitch;
+    const int wq = w - q;
+    const bool q_ok = wq >= L.aw0, q1_ok = wq - 1 >= L.aw0;
+    const uint32_t a0 = row[w];
+    const uint32_t a1 = up_ok ? up[w] : 0u;
+    uint32_t a2 = q_ok ? row[wq] : 0u;
+    uint32_t a3 = (up_ok && q_ok) ? up[wq] : 0u;
     if (r) {
-      a2 = (a2 << r) | (L.get(i, w - q - 1) >> (32 - r));
-      a3 = (a3 << r) | (L.get(i - d, w - q - 1) >> (32 - r));
+      a2 = (a2 << r) | ((q1_ok ? row[wq - 1] : 0u) >> (32 - r));
+      a3 = (a3 << r) | ((up_ok && q1_ok ? up[wq - 1] : 0u) >> (32 - r));
     }
-    const int64_t valid = n - 32 * (int64_t)w;
-    const uint32_t cm = valid >= 32 ? 0xffffffffu : (valid <= 0 ? 0u : ((1u << valid) - 1u));
-    const uint32_t v = a0 & a1 & a2 & a3 & cm;
+    const uint32_t v = a0 & a1 & a2 & a3 & (w == wlast ? lastmask : 0xffffffffu);
     if (write) O.p[(i - O.r0) * O.pitch + (w - O.w0)] = v;
     if (v) {
       rmin = min(rmin, i);
@@ -1336,8 +1346,10 @@ __global__ void __launch_bounds__(1024, 1) k_fixup_bits_one(const Job job, int64
                       (int)blockIdx.x, sync);
 }
 
-// Batch: one block per (matrix, rank) task, larger teams first; matrices
-// without bitplane scratch go to the strip fix-up.
+// Batch: one block per (matrix, rank) task, larger teams first (the
+// hardware hands blocks to free SMs, which balances the uneven boxes better
+// than blocks that loop over several matrices); matrices without bitplane
+// scratch go to the strip fix-up.
 struct FixTask {
   int32_t job, rank, size, pad;
 };
