@@ -934,25 +934,33 @@ __device__ __forceinline__ Plane build_s32(const Job& j, const BitGeo& g, uint32
     in[rr * Wv + cc] = input_word<FMT>(j, pa + rr, wa - 1 + cc);
   });
   tm.barrier();
-  // 2. vertical: V_32(i, w) = AND of the 32 rows ending at i, by doubling
-  //    V_2k(i) = V_k(i) & V_k(i-k) over rows [pa, rhi) (5 passes, ping-pong
-  //    between `in` and `vb`, ending in `vb`).  Rows above pa read as zeros,
-  //    so V_k is exact on rows >= pa + k - 1, which covers every row >= ra
-  //    (pa = ra - 31, or pa = 0 at the matrix top where the zeros are real).
-  {
-    uint32_t* src = in;
-    uint32_t* dst = vb;
-    for (int k = 1; k < 32; k *= 2) {
-      for_cells(tm, RP, Wv, [&](int rr, int cc) {
-        const int e = rr * Wv + cc;
-        dst[e] = rr >= k ? src[e] & src[e - k * Wv] : 0u;
-      });
-      tm.barrier();
-      uint32_t* t = src;
-      src = dst;
-      dst = t;
+  // 2. vertical: V_32(i, w) = AND of the 32 rows ending at i.  Rows are taken
+  //    in blocks of 32 counted from pa; one thread per block and word column
+  //    stores the running AND from the block's top (prefix, into `vb`) and,
+  //    in place, from its bottom (suffix, into `in`).  Then V_32(i) is
+  //    suffix(i - 31) & prefix(i), or the block's whole prefix when i ends a
+  //    block.  Rows above pa only matter when pa is the matrix top, where
+  //    they are zeros.
+  const int nb = (RP + 31) / 32;
+  for_cells(tm, nb, Wv, [&](int bk, int cc) {
+    const int r0 = 32 * bk, rows = min(32, RP - r0);
+    uint32_t acc = 0xffffffffu;
+    for (int k = 0; k < rows; ++k) {
+      acc &= in[(r0 + k) * Wv + cc];
+      vb[(r0 + k) * Wv + cc] = acc;
     }
-  }
+    acc = 0xffffffffu;
+    for (int k = rows - 1; k >= 0; --k) {
+      acc &= in[(r0 + k) * Wv + cc];
+      in[(r0 + k) * Wv + cc] = acc;
+    }
+  });
+  tm.barrier();
+  auto v32 = [&](int rr, int cc) -> uint32_t {
+    if ((rr & 31) == 31) return vb[rr * Wv + cc];
+    if (rr < 31) return 0u;
+    return in[(rr - 31) * Wv + cc] & vb[rr * Wv + cc];
+  };
   // 3. horizontal: S_32 = AND of 32 consecutive V_32 bits ending at each
   //    cell, on rows [ra, rhi) x words [wa, whi)
   Plane s32{s32buf, ra, wa, W1, 0, 0, 0, 0};
@@ -960,7 +968,7 @@ __device__ __forceinline__ Plane build_s32(const Job& j, const BitGeo& g, uint32
   pb.begin();
   for_cells(tm, R1, W1, [&](int rr, int cc) {
     const int vr = rr + (ra - pa);  // row of V_32 in its [pa, rhi) layout
-    const uint32_t x = vb[vr * Wv + cc + 1], y = vb[vr * Wv + cc];
+    const uint32_t x = v32(vr, cc + 1), y = v32(vr, cc);
     unsigned long long z = ((unsigned long long)x << 32) | y;
     z &= z << 1;
     z &= z << 2;
