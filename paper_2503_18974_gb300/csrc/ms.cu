@@ -298,6 +298,7 @@ int fix_team_size(int64_t cells, int cap, int shift = 23) {
 int64_t bitfix_words(const Job& j) { return j.m > 0 && j.n > 0 ? 3 * j.m * ((j.n + 31) / 32 + 2) : 0; }
 constexpr int64_t kBitfixCapWords = (int64_t)1 << 30;  // 4 GiB
 constexpr size_t kBitsFixSmemBytes = 200 * 1024;         // planes of small boxes
+constexpr int kFixClusterBlocks = 8;  // a single large matrix's fix-up cluster (portable size)
 
 
 
@@ -415,11 +416,30 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
       const size_t sm = kBitsFixSmemBytes;
       if (allow_smem((const void*)ms::k_fixup_bits_one<FMT>, sm) != cudaSuccess)
         return cudaGetLastError();
-      const int team = fix_team_size(j.m * j.n, std::min(16, ctx->sms));
-      if (team > 1 && cudaMemsetAsync(ctx->d_sync1, 0, sizeof(ms::TeamSync), s) != cudaSuccess)
-        return cudaGetLastError();
-      ms::k_fixup_bits_one<FMT><<<team, 1024, sm, s>>>(j, (int64_t)(sm / 4),
-                                                       team > 1 ? ctx->d_sync1 : nullptr);
+      const int team = fix_team_size(j.m * j.n, std::min(kFixClusterBlocks, ctx->sms));
+      if (team > 1) {
+        // one thread-block cluster: the blocks share every pass over planes
+        // in global memory and meet at the hardware cluster barrier
+        if (cudaMemsetAsync(ctx->d_sync1, 0, sizeof(ms::TeamSync), s) != cudaSuccess)
+          return cudaGetLastError();
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)team);
+        cfg.blockDim = dim3(1024);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)team;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, ms::k_fixup_bits_one<FMT>, j, (int64_t)0,
+                                                 ctx->d_sync1, 1);
+        if (e != cudaSuccess) return e;
+      } else {
+        ms::k_fixup_bits_one<FMT><<<1, 1024, sm, s>>>(j, (int64_t)(sm / 4), nullptr, 0);
+      }
     } else {
       const bool levels = DPMAP && j.bits_scratch && !j.test_hold;
       if (levels) {

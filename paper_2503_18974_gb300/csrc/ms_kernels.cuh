@@ -698,9 +698,18 @@ struct Team {
   int32_t* status;
   unsigned int passed;  // barriers passed
   bool gave_up;
+  bool cluster;         // the team is one thread-block cluster: hardware barrier
   __device__ __forceinline__ int thread() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
   __device__ __forceinline__ int threads() const { return size * (int)blockDim.x; }
   __device__ __forceinline__ void barrier() {
+    if (size > 1 && cluster) {
+      // every thread of every block of the cluster; release/acquire order
+      // the team's global-memory plane writes before the next pass's reads
+      asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                   "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+      ++passed;
+      return;
+    }
     __syncthreads();
     if (size > 1) {
       if (threadIdx.x == 0) {
@@ -1010,16 +1019,17 @@ __device__ __forceinline__ void pass_box_init(int (*s_box)[4]) {
 template <int FMT>
 __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int clo, int chi,
                                            uint32_t* smem, int64_t smem_words, int team_size,
-                                           int rank, TeamSync* sync) {
+                                           int rank, TeamSync* sync, bool cluster = false) {
   __shared__ unsigned long long s_first;
   __shared__ int s_box[3][4];
   const BitGeo g(rlo, rhi, clo, chi);
   const int wlo = g.wlo, whi = g.whi;
   const bool fits = smem && 2 * (int64_t)g.RP * g.Wv + (int64_t)g.R1 * g.W1 <= smem_words;
-  const bool alone = fits || !sync || team_size <= 1;
+  // (a cluster team always works together: its barrier counts every block)
+  const bool alone = !cluster && (fits || !sync || team_size <= 1);
   if (alone && rank != 0) return;
   Team tm{alone ? 1 : team_size, alone ? 0 : rank, alone ? nullptr : sync, &j.st->status, 0u,
-          false};
+          false, cluster && !alone};
   PassBox pb{s_box, 0, &tm};
   pass_box_init(s_box);
   if (threadIdx.x == 0) {
@@ -1126,7 +1136,7 @@ template <int FMT>
 __device__ __forceinline__ void fixup_dp_levels(const Job& j, int rlo, int rhi, int clo, int chi,
                                                 uint32_t* smem, int64_t smem_words) {
   __shared__ int s_box[3][4];
-  Team tm{1, 0, nullptr, &j.st->status, 0u, false};
+  Team tm{1, 0, nullptr, &j.st->status, 0u, false, false};
   PassBox pb{s_box, 0, &tm};
   pass_box_init(s_box);
   LevelTab* tab = reinterpret_cast<LevelTab*>(j.bits_scratch);
@@ -1326,7 +1336,8 @@ __device__ __forceinline__ void fixup_job(const Job& j, bool after_levels = true
 // Size-only fix-up of one matrix by bitplane growth, then its result.
 template <int FMT>
 __device__ __forceinline__ void fixup_bits_job(const Job& j, uint32_t* smem, int64_t smem_words,
-                                               int team_size, int rank, TeamSync* sync) {
+                                               int team_size, int rank, TeamSync* sync,
+                                               bool cluster = false) {
   __shared__ int32_t sbox[4];
   if (threadIdx.x == 0) {
     const volatile int32_t* b = j.st->box;
@@ -1338,20 +1349,20 @@ __device__ __forceinline__ void fixup_bits_job(const Job& j, uint32_t* smem, int
   __syncthreads();
   if (sbox[1] > sbox[0] && sbox[3] > sbox[2])
     fixup_bits<FMT>(j, sbox[0], sbox[1], sbox[2], sbox[3], smem, smem_words, team_size, rank,
-                    sync);
+                    sync, cluster);
   if (rank != 0) return;
   __syncthreads();
   finalize_job(j);
 }
 
 // One matrix: a team of gridDim.x blocks (`sync` zeroed before the launch when
-// there are several).
+// there are several); cluster != 0 when the grid is one thread-block cluster.
 template <int FMT>
 __global__ void __launch_bounds__(1024, 1) k_fixup_bits_one(const Job job, int64_t smem_words,
-                                                            TeamSync* sync) {
+                                                            TeamSync* sync, int cluster) {
   extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
   fixup_bits_job<FMT>(job, reinterpret_cast<uint32_t*>(ms_dyn_smem), smem_words, (int)gridDim.x,
-                      (int)blockIdx.x, sync);
+                      (int)blockIdx.x, sync, cluster != 0);
 }
 
 // Batch: one block per (matrix, rank) task, larger teams first (the

@@ -82,22 +82,24 @@ def test_serve_refuses_requests_that_can_never_fit(ms):
 
 
 def test_serve_continuous_batching_overlaps(ms):
-    """A second wave submitted while the first runs is batched separately and
-    runs on the other stream, overlapping it."""
+    """A second wave submitted while the first wave's batch is on the device
+    is batched separately and runs on another stream, overlapping it."""
     srv = ms.Server(0, memory_budget=1 << 30, streams=2, max_batch=64)
     wave = []
     for i in range(2):
-        a = gen.bernoulli_u8(4096, 4096, 0.9, seed=40 + i)
-        a[1000:2800, 500:2300] = 1  # a large square: the exact fix-up runs for a while
-        wave.append(gen.pack_bits(a, 4096))
-    first = [srv.submit(wave[0], n=4096) for _ in range(4)]
-    time.sleep(0.002)
-    second = [srv.submit(wave[1], n=4096) for _ in range(4)]
+        a = gen.bernoulli_u8(8192, 8192, 0.9, seed=40 + i)
+        a[1000:4000, 500:3500] = 1  # a large square: the exact fix-up runs for a while
+        wave.append(gen.pack_bits(a, 8192))
+    first = [srv.submit(wave[k % 2], n=8192) for k in range(12)]
+    t0 = time.time()
+    while srv.stats()["batches"] < 1 and time.time() - t0 < 10:
+        time.sleep(0.0002)
+    second = [srv.submit(wave[1], n=8192) for _ in range(4)]
     srv.wait_all()
     done = {c["id"]: c for c in srv.poll(100)}
     stats = srv.stats()
     srv.close()
     assert stats["batches"] >= 2
-    assert all(done[i]["result"][0] == 1800 for i in first + second)
+    assert all(done[i]["result"][0] == 3000 for i in first + second)
     t_done_first = min(done[i]["t_done"] for i in first)
     assert any(done[i]["t_launch"] < t_done_first for i in second) or stats["peak_inflight"] >= 2
