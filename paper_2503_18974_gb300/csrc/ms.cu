@@ -302,6 +302,28 @@ constexpr int kFixClusterBlocks = 8;  // a single large matrix's fix-up cluster 
 
 
 
+// Launch configuration of one `team`-block thread-block cluster of 1024
+// threads with no dynamic shared memory; clears the context's team barrier
+// state first (stream-ordered).
+cudaError_t cluster_config(ms_ctx* ctx, int team, cudaStream_t s, cudaLaunchConfig_t& cfg,
+                           cudaLaunchAttribute& attr) {
+  const cudaError_t e = cudaMemsetAsync(ctx->d_sync1, 0, sizeof(ms::TeamSync), s);
+  if (e != cudaSuccess) return e;
+  cfg = cudaLaunchConfig_t{};
+  cfg.gridDim = dim3((unsigned)team);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  attr = cudaLaunchAttribute{};
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = (unsigned)team;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaSuccess;
+}
+
 ms_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MS_OK : MS_ERR_CUDA; }
 
 template <typename T>
@@ -420,20 +442,10 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
       if (team > 1) {
         // one thread-block cluster: the blocks share every pass over planes
         // in global memory and meet at the hardware cluster barrier
-        if (cudaMemsetAsync(ctx->d_sync1, 0, sizeof(ms::TeamSync), s) != cudaSuccess)
-          return cudaGetLastError();
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)team);
-        cfg.blockDim = dim3(1024);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)team;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute attr;
+        const cudaError_t e0 = cluster_config(ctx, team, s, cfg, attr);
+        if (e0 != cudaSuccess) return e0;
         const cudaError_t e = cudaLaunchKernelEx(&cfg, ms::k_fixup_bits_one<FMT>, j, (int64_t)0,
                                                  ctx->d_sync1, 1);
         if (e != cudaSuccess) return e;
@@ -449,7 +461,19 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
         const size_t smb = kBitsFixSmemBytes;
         if (allow_smem((const void*)ms::k_fixup_dp_levels<FMT>, smb) != cudaSuccess)
           return cudaGetLastError();
-        ms::k_fixup_dp_levels<FMT><<<1, 1024, smb, s>>>(j, (int64_t)(smb / 4));
+        const int team = fix_team_size(j.m * j.n, std::min(kFixClusterBlocks, ctx->sms));
+        if (team > 1) {
+          // a large matrix: one thread-block cluster builds the levels
+          cudaLaunchConfig_t cfg;
+          cudaLaunchAttribute attr;
+          const cudaError_t e0 = cluster_config(ctx, team, s, cfg, attr);
+          if (e0 != cudaSuccess) return e0;
+          const cudaError_t e =
+              cudaLaunchKernelEx(&cfg, ms::k_fixup_dp_levels<FMT>, j, (int64_t)0, ctx->d_sync1);
+          if (e != cudaSuccess) return e;
+        } else {
+          ms::k_fixup_dp_levels<FMT><<<1, 1024, smb, s>>>(j, (int64_t)(smb / 4), nullptr);
+        }
         ms::k_fixup_dp_cells<<<4 * ctx->sms, 256, 0, s>>>(j);
       }
       const size_t sm = ring_bytes(ms::kFixWarps * 32);

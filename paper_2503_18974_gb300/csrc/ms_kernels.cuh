@@ -802,6 +802,16 @@ __device__ __forceinline__ void box_reset(int* b) {
   b[2] = 0x7fffffff;
   b[3] = -1;
 }
+// A team's boxes in global memory are kept so that all-zero bytes mean the
+// empty box (the launch's memset prepares pass 0 with no reset that could
+// race another block's first fold): 0x7fffffff - min and max + 1, both
+// folded with atomicMax.
+__device__ __forceinline__ void gbox_reset(int* b) {
+  b[0] = 0;
+  b[1] = 0;
+  b[2] = 0;
+  b[3] = 0;
+}
 struct PassBox {
   int (*slot)[4];  // shared [3][4]: row min, row max, word min, word max
   int k;
@@ -809,7 +819,7 @@ struct PassBox {
   __device__ __forceinline__ void begin() const {
     if (threadIdx.x == 0) {
       box_reset(slot[(k + 1) % 3]);
-      if (tm->size > 1 && tm->rank == 0) box_reset(tm->sync->box[(k + 1) % 3]);
+      if (tm->size > 1 && tm->rank == 0) gbox_reset(tm->sync->box[(k + 1) % 3]);
     }
   }
   // all threads of the team; returns [r0, r1) x [w0, w1) (empty: r1 <= r0)
@@ -829,17 +839,17 @@ struct PassBox {
       __syncthreads();
       int* g = tm->sync->box[k % 3];
       if (threadIdx.x == 0 && b[1] >= 0) {
-        atomicMin(g + 0, b[0]);
-        atomicMax(g + 1, b[1]);
-        atomicMin(g + 2, b[2]);
-        atomicMax(g + 3, b[3]);
+        atomicMax(g + 0, 0x7fffffff - b[0]);
+        atomicMax(g + 1, b[1] + 1);
+        atomicMax(g + 2, 0x7fffffff - b[2]);
+        atomicMax(g + 3, b[3] + 1);
       }
       tm->barrier();
       if (threadIdx.x == 0) {
-        b[0] = *reinterpret_cast<volatile int*>(g + 0);
-        b[1] = *reinterpret_cast<volatile int*>(g + 1);
-        b[2] = *reinterpret_cast<volatile int*>(g + 2);
-        b[3] = *reinterpret_cast<volatile int*>(g + 3);
+        b[0] = 0x7fffffff - *reinterpret_cast<volatile int*>(g + 0);
+        b[1] = *reinterpret_cast<volatile int*>(g + 1) - 1;
+        b[2] = 0x7fffffff - *reinterpret_cast<volatile int*>(g + 2);
+        b[3] = *reinterpret_cast<volatile int*>(g + 3) - 1;
       }
     }
     __syncthreads();
@@ -1035,7 +1045,6 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
   if (threadIdx.x == 0) {
     s_first = ~0ull;
     if (!alone && rank == 0) {
-      box_reset(sync->box[0]);
       sync->first = ~0ull;
     }
   }
@@ -1131,14 +1140,20 @@ __device__ __forceinline__ uint32_t level_bit(const LevelRec& L, const uint32_t*
 }
 
 // Builds S_32 and the doubling levels of box [rlo, rhi) x [clo, chi).  The
-// input and vertical buffers use shared memory when they fit.
+// input and vertical buffers use shared memory when they fit.  A
+// thread-block cluster (cluster_size > 1, `sync` cleared before the launch)
+// shares every pass, with all planes in global memory.
 template <int FMT>
 __device__ __forceinline__ void fixup_dp_levels(const Job& j, int rlo, int rhi, int clo, int chi,
-                                                uint32_t* smem, int64_t smem_words) {
+                                                uint32_t* smem, int64_t smem_words,
+                                                int cluster_size, int rank, TeamSync* sync) {
   __shared__ int s_box[3][4];
-  Team tm{1, 0, nullptr, &j.st->status, 0u, false, false};
+  const bool cl = cluster_size > 1;
+  Team tm{cl ? cluster_size : 1, cl ? rank : 0, cl ? sync : nullptr, &j.st->status, 0u, false,
+          cl};
   PassBox pb{s_box, 0, &tm};
   pass_box_init(s_box);
+  if (cl) smem = nullptr;
   LevelTab* tab = reinterpret_cast<LevelTab*>(j.bits_scratch);
   uint32_t* base = j.bits_scratch + kTabWords;
   const int64_t avail = 3 * j.m * ((j.n + 31) / 32 + 2) - kTabWords;
@@ -1156,7 +1171,8 @@ __device__ __forceinline__ void fixup_dp_levels(const Job& j, int rlo, int rhi, 
   }
   if (off + (int64_t)g.R1 * g.W1 > avail) return;  // does not fit: table stays empty
   Plane cur = build_s32<FMT>(j, g, in, vb, base + off, pb);
-  if (threadIdx.x == 0)
+  const bool writer = threadIdx.x == 0 && tm.rank == 0;
+  if (writer)
     tab->lv[0] = LevelRec{off, g.ra, g.wa, g.W1, cur.ar0, cur.ar1, cur.aw0, cur.aw1, 0};
   off += (int64_t)g.R1 * g.W1;
   int nl = 1, a = 32;
@@ -1171,31 +1187,36 @@ __device__ __forceinline__ void fixup_dp_levels(const Job& j, int rlo, int rhi, 
     Plane nxt{base + off, r0, w0, w1 - w0, 0, 0, 0, 0};
     grow_pass(cur, nxt, r1, w1, a, j.n, true, nullptr, pb);
     if (nxt.empty()) break;
-    if (threadIdx.x == 0)
+    if (writer)
       tab->lv[nl] = LevelRec{off, r0, w0, w1 - w0, nxt.ar0, nxt.ar1, nxt.aw0, nxt.aw1, 0};
     off += size;
     ++nl;
     a *= 2;
     cur = nxt;
   }
-  if (threadIdx.x == 0) tab->n = nl;
+  if (writer) tab->n = nl;
 }
 
+// One block, or one thread-block cluster of gridDim.x blocks (`sync` cleared
+// before the launch).
 template <int FMT>
-__global__ void __launch_bounds__(1024, 1) k_fixup_dp_levels(const Job job, int64_t smem_words) {
+__global__ void __launch_bounds__(1024, 1) k_fixup_dp_levels(const Job job, int64_t smem_words,
+                                                             TeamSync* sync) {
   extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
   __shared__ int32_t sbox[4];
   if (threadIdx.x == 0) {
-    reinterpret_cast<LevelTab*>(job.bits_scratch)->n = 0;
-    sbox[0] = job.st->box[0];
-    sbox[1] = job.st->box[1];
-    sbox[2] = job.st->box[2];
-    sbox[3] = job.st->box[3];
+    if (blockIdx.x == 0) reinterpret_cast<LevelTab*>(job.bits_scratch)->n = 0;
+    const volatile int32_t* b = job.st->box;
+    sbox[0] = b[0];
+    sbox[1] = b[1];
+    sbox[2] = b[2];
+    sbox[3] = b[3];
   }
   __syncthreads();
   if (sbox[1] > sbox[0] && sbox[3] > sbox[2])
     fixup_dp_levels<FMT>(job, sbox[0], sbox[1], sbox[2], sbox[3],
-                         reinterpret_cast<uint32_t*>(ms_dyn_smem), smem_words);
+                         reinterpret_cast<uint32_t*>(ms_dyn_smem), smem_words, (int)gridDim.x,
+                         (int)blockIdx.x, sync);
 }
 
 // Exact dp of the box cells from the levels (grid-stride over S_32's active

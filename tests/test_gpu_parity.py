@@ -142,6 +142,23 @@ def test_large_boxes_shared_by_block_teams(ctx):
     assert ctx.batch(mats).cpu().tolist() == exps
 
 
+def test_dp_map_levels_by_cluster(ctx):
+    """A large matrix's dp-map levels are built by a cluster of blocks: the
+    whole map against the oracle, with the flagged box spanning most rows."""
+    m, n, s = 6000, 6000, 2100
+    a = gen.bernoulli_u8(m, n, 0.92, seed=9200)
+    a[300:300 + s, 3000:3000 + s] = 1
+    a[3500:3500 + 900, 100:100 + 900] = 1
+    want, ref = oracle.dp(a, want_map=True)
+    assert want[0] == s
+    dp, res = ctx.dp_map(to_dev(a))
+    assert res.cpu().tolist() == list(want) + [0]
+    assert np.array_equal(dp.cpu().numpy(), ref)
+    dpb, resb = ctx.dp_map(bits_dev(a, n, pad=3), n=n)
+    assert resb.cpu().tolist() == list(want) + [0]
+    assert np.array_equal(dpb.cpu().numpy(), ref)
+
+
 def test_squares_on_tile_edges(ctx):
     ctx.set_tuning(band_rows=64)
     try:
