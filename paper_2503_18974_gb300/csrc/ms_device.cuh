@@ -226,6 +226,82 @@ __device__ __forceinline__ uint32_t pair_mask(const Cells<P, MS_BITS32>& lo,
   return prmt(w << (15 - (k & 15)), 0u, 0xBB99u);
 }
 
+// ---- size-only tile pass in dp units (fp16x2) ------------------------------
+// Inside a tile's window every dp_w is at most the window's width, 32*P <= 1024
+// columns, so the window's dp values themselves are exact in fp16 (whose
+// integers are exact up to 2048).  On a one dp = 1 + min(up, left, diag), on a
+// zero 0: with v = 1.0 or 0.0 per half that is v * m + v after two packed
+// minima m, one fma.f16x2, which issues on the FMA pipe while the minima,
+// prmt and lop3 of the row-unit form all share the (half-rate) ALU pipe.
+// Non-negative fp16 values order like their bit patterns, so min.u16x2 and
+// max.u16x2 on the bits are exact minima and maxima.
+constexpr uint32_t kOneH = 0x3C00u;        // fp16 1.0
+constexpr uint32_t kHaloH2 = 0x50005000u;  // fp16 32.0 (= kHalo) in both halves
+static_assert(kHalo == 32, "kHaloH2 encodes kHalo");
+
+__device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t imul(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+// The integer held by fp16 bits `h` (a whole number 0..2047): IEEE binary16
+// stores 2^(e-15) * (1 + f/1024), so the value is (1024 + f) >> (25 - e).
+__device__ __forceinline__ int h16_int(uint32_t h) {
+  h &= 0xffffu;
+  return h == 0u ? 0 : (int)((1024u | (h & 1023u)) >> (25u - (h >> 10)));
+}
+
+// 0/1 bytes scaled to 0x3C (the high byte of fp16 1.0): one multiply per word
+// (no carries between bytes while every byte is 0 or 1).  Every raw word is
+// ORed into `seen`, so the caller can tell afterwards whether that held.
+template <int P>
+__device__ __forceinline__ Cells<P, MS_U8> cells_h01(const Raw<P, MS_U8>& r, uint32_t& seen) {
+  Cells<P, MS_U8> c;
+#pragma unroll
+  for (int i = 0; i < Raw<P, MS_U8>::W; ++i) {
+    c.w[i] = imul(r.w[i], 0x3Cu);
+    seen |= r.w[i];
+  }
+  return c;
+}
+// Pair k as fp16x2 ones: byte 1 <- low tile's byte, byte 3 <- high tile's
+// byte, bytes 0 and 2 <- their (clear) sign bits replicated.
+template <int P>
+__device__ __forceinline__ uint32_t pair_one(const Cells<P, MS_U8>& lo, const Cells<P, MS_U8>& hi,
+                                             int k) {
+  const uint32_t b = (uint32_t)(k & 3);
+  const uint32_t sel = (8u | b) | (b << 4) | ((12u | b) << 8) | ((4u | b) << 12);
+  return prmt(lo.w[k >> 2], hi.w[k >> 2], sel);
+}
+// MS_BITS32: columns 0..15 of both tiles interleaved by halves (and the same
+// shifted right by 5), then columns 16..31 likewise; pair k is one AND and
+// one multiply that moves bit j of each half to the fp16 1.0 pattern
+// (0x3C00 = 15 << 10).
+struct BitsH {
+  uint32_t c[4];
+};
+template <int P>
+__device__ __forceinline__ BitsH bits_h(const Cells<P, MS_BITS32>& lo,
+                                        const Cells<P, MS_BITS32>& hi) {
+  BitsH h;
+  h.c[0] = prmt(lo.bits, hi.bits, 0x5410u);
+  h.c[1] = h.c[0] >> 5;
+  h.c[2] = prmt(lo.bits, hi.bits, 0x7632u);
+  h.c[3] = h.c[2] >> 5;
+  return h;
+}
+__device__ __forceinline__ uint32_t pair_one(const BitsH& h, int k) {
+  const int j = k & 15;
+  const int g = (k >> 4) * 2 + (j > 10 ? 1 : 0);
+  const int s = j > 10 ? j - 5 : j;
+  return imul(h.c[g] & (0x00010001u << s), kOneH >> s);
+}
+
 // ---- results --------------------------------------------------------------
 
 struct Best {

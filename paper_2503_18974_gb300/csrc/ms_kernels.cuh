@@ -315,14 +315,18 @@ __device__ __forceinline__ bool run_tiles(const Tile& ta, const Tile& tb, int32_
   uint32_t seen = 0;  // B01: OR of every raw input word
   const int lane = threadIdx.x & 31;
   constexpr uint32_t kB2 = kBias * 0x10001u;
+  // size-only tile pass on cells known to be 0/1: dp units in fp16 (hfma2)
+  constexpr bool H = MODE == 0 && !DPMAP && !EMIT && (B01 || FMT == MS_BITS32);
+  constexpr uint32_t kInit = H ? 0u : kB2;  // the value above / left of the window
+  constexpr uint32_t kHaloCmp2 = H ? kHaloH2 : (uint32_t)kHalo * 0x10001u;
   constexpr int D = RingGeom<P, FMT>::kDepth;  // rows of input in flight per lane
   const int nmax = max(ta.nrows, tb.nrows);
   const int nsteps = nmax + 31;
 
   uint32_t Ap[P];  // A of the lane's columns on the last row computed
 #pragma unroll
-  for (int k = 0; k < P; ++k) Ap[k] = kB2;
-  uint32_t pubL = kB2, pubD = kB2;  // A of the lane's last column: this row, the row above
+  for (int k = 0; k < P; ++k) Ap[k] = kInit;
+  uint32_t pubL = kInit, pubD = kInit;  // A of the lane's last column: this row, the row above
   uint32_t carryA_prev = kBias;  // fix-up: A of the left strip's last column, previous row
   uint4 cq = make_uint4(0u, 0u, 0u, 0u);  // fix-up: the next carries, 16 bits per row
   bool gave_up = false;
@@ -333,7 +337,6 @@ __device__ __forceinline__ bool run_tiles(const Tile& ta, const Tile& tb, int32_
   ba.big_c0 = bb.big_c0 = 0x7fffffffffffffffll;
   ba.big_c1 = bb.big_c1 = -1;
   uint32_t best2 = 0;  // best dp per half so far (packed)
-  constexpr uint32_t kHalo2 = (uint32_t)kHalo * 0x10001u;
   const int64_t cola = ta.wc0 + (int64_t)P * lane;
   const int64_t colb = tb.wc0 + (int64_t)P * lane;
   // a lane chunk counts when it reaches a counted column: in the fix-up the
@@ -373,7 +376,10 @@ __device__ __forceinline__ bool run_tiles(const Tile& ta, const Tile& tb, int32_
       rda.read(d, rlo);
       rdb.read(d, rhi);
       Cells<P, FMT> clo, chi;
-      if constexpr (B01) {
+      if constexpr (B01 && H) {
+        clo = cells_h01<P>(rlo, seen);
+        chi = cells_h01<P>(rhi, seen);
+      } else if constexpr (B01) {
         clo = cells_of01<P>(rlo, seen);
         chi = cells_of01<P>(rhi, seen);
       } else {
@@ -386,8 +392,8 @@ __device__ __forceinline__ bool run_tiles(const Tile& ta, const Tile& tb, int32_
         if (lane == 0) {
           // left window edge: a zero column (dp = 0, so A = I on this row and
           // I - 1 on the row above)
-          al = I2;
-          ad = I2 - 0x10001u;
+          al = H ? 0u : I2;
+          ad = H ? 0u : I2 - 0x10001u;
           if constexpr (MODE == 1) {
             if (io.carry_in) {
               if ((ir & 7) == 0) {
@@ -425,16 +431,37 @@ __device__ __forceinline__ bool run_tiles(const Tile& ta, const Tile& tb, int32_
         // decrement by 0x00010001 never borrows across halves.  (Selecting I
         // before the last max would shorten the chain along the row to two
         // operations, but measured slower.)
-        uint32_t rmin = 0xffffffffu;
+        uint32_t rbest;  // H: the row's largest dp (fp16 bits), else its smallest A
+        if constexpr (H) {
+          uint32_t rmax = 0u;
+          BitsH hb;
+          if constexpr (FMT == MS_BITS32) hb = bits_h<P>(clo, chi);
 #pragma unroll
-        for (int k = 0; k < P; ++k) {
-          const uint32_t msk = pair_mask<P>(clo, chi, k);
-          const uint32_t up = Ap[k];
-          const uint32_t t = vmax2(vmax2(up, ad), al - 0x00010001u);
-          ad = up;
-          al = select_bits(t, I2, msk);
-          Ap[k] = al;
-          rmin = vmin2(rmin, al);
+          for (int k = 0; k < P; ++k) {
+            uint32_t v;
+            if constexpr (FMT == MS_BITS32) v = pair_one(hb, k);
+            else v = pair_one<P>(clo, chi, k);
+            const uint32_t up = Ap[k];
+            const uint32_t mn = vmin2(vmin2(up, ad), al);
+            ad = up;
+            al = hfma2(v, mn, v);
+            Ap[k] = al;
+            rmax = vmax2(rmax, al);
+          }
+          rbest = rmax;
+        } else {
+          uint32_t rmin = 0xffffffffu;
+#pragma unroll
+          for (int k = 0; k < P; ++k) {
+            const uint32_t msk = pair_mask<P>(clo, chi, k);
+            const uint32_t up = Ap[k];
+            const uint32_t t = vmax2(vmax2(up, ad), al - 0x00010001u);
+            ad = up;
+            al = select_bits(t, I2, msk);
+            Ap[k] = al;
+            rmin = vmin2(rmin, al);
+          }
+          rbest = rmin;
         }
         pubL = al;
         pubD = ad;  // A of this lane's last column, row above
@@ -449,16 +476,17 @@ __device__ __forceinline__ bool run_tiles(const Tile& ta, const Tile& tb, int32_
         }
 
         // this row's best dp per half (I >= A, so the packed subtraction is
-        // exact), kept only for counted rows and columns
+        // exact), kept only for counted rows and columns; H: as fp16 bits,
+        // which order like the values
         const uint32_t rowmask2 = (ir >= ta.cnt_ir0 ? 0x0000ffffu : 0u) |
                                   (ir >= tb.cnt_ir0 ? 0xffff0000u : 0u);
-        const uint32_t d2 = (I2 - rmin) & colmask2 & rowmask2;
+        const uint32_t d2 = (H ? rbest : I2 - rbest) & colmask2 & rowmask2;
         if (vmax2(d2, best2) != best2) {
           const uint32_t dlo = d2 & 0xffffu, dhi = d2 >> 16;
           if (dlo > (best2 & 0xffffu)) {
-            ba.val = (int)dlo;
+            ba.val = H ? h16_int(dlo) : (int)dlo;
             ba.row = (int32_t)(ta.wr0 + ir);
-            const uint32_t target = I - dlo;
+            const uint32_t target = H ? dlo : I - dlo;
             int kk = 0;
 #pragma unroll
             for (int k = P - 1; k >= 0; --k)
@@ -466,9 +494,9 @@ __device__ __forceinline__ bool run_tiles(const Tile& ta, const Tile& tb, int32_
             ba.col = (int32_t)(cola + kk);
           }
           if (dhi > (best2 >> 16)) {
-            bb.val = (int)dhi;
+            bb.val = H ? h16_int(dhi) : (int)dhi;
             bb.row = (int32_t)(tb.wr0 + ir);
-            const uint32_t target = I - dhi;
+            const uint32_t target = H ? dhi : I - dhi;
             int kk = 0;
 #pragma unroll
             for (int k = P - 1; k >= 0; --k)
@@ -490,8 +518,8 @@ __device__ __forceinline__ bool run_tiles(const Tile& ta, const Tile& tb, int32_
           }
         }
         // rows and lane chunks holding a value above the halo: the fix-up box
-        if (vmax2(d2, kHalo2) != kHalo2) {
-          if ((d2 & 0xffffu) > (uint32_t)kHalo) {
+        if (vmax2(d2, kHaloCmp2) != kHaloCmp2) {
+          if ((d2 & 0xffffu) > (kHaloCmp2 & 0xffffu)) {
             if (ba.big_r0 == 0x7fffffff) {
               ba.big_r0 = (int32_t)(ta.wr0 + ir);
               ba.big_c0 = cola;
@@ -499,7 +527,7 @@ __device__ __forceinline__ bool run_tiles(const Tile& ta, const Tile& tb, int32_
             }
             ba.big_r1 = (int32_t)(ta.wr0 + ir + 1);
           }
-          if ((d2 >> 16) > (uint32_t)kHalo) {
+          if ((d2 >> 16) > (kHaloCmp2 >> 16)) {
             if (bb.big_r0 == 0x7fffffff) {
               bb.big_r0 = (int32_t)(tb.wr0 + ir);
               bb.big_c0 = colb;
