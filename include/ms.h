@@ -234,8 +234,12 @@ double ms_server_now(void);
  * left), `packed_path` selects, for MS_BITS32 size-only work, the bitplane
  * erosion search (1) or the byte-style tile kernel on unpacked bits (0).
  * `lane_cols` = columns each lane of a warp owns in a tile (1, 2, 4, 8, 16
- * or 32; a tile is 32 * lane_cols columns wide).
- * 0 for band_rows or lane_cols = choose automatically from the matrix size. */
+ * or 32; a tile is 32 * lane_cols columns wide).  `tile_kind` selects the
+ * size-only tile pass of ms_max_square: 1 = the dp recurrence on two tiles
+ * per warp (16-bit lanes), 2 = bitplane tiles (one tile of 1024 columns per
+ * warp, 32 cells per word, doubling and threshold tests).
+ * 0 for band_rows, lane_cols or tile_kind = choose automatically from the
+ * matrix size. */
 typedef struct {
   int32_t band_rows;
   int32_t packed_path;
@@ -245,7 +249,8 @@ typedef struct {
    * MS_ERR_TIMEOUT; later calls with the hook off are unaffected. */
   int32_t test_hold_carries;
   int32_t lane_cols;
-  int32_t reserved[4];
+  int32_t tile_kind;
+  int32_t reserved[3];
 } ms_tuning;
 
 ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t);

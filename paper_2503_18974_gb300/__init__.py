@@ -68,7 +68,7 @@ class _Matrix(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("band_rows", ctypes.c_int32), ("packed_path", ctypes.c_int32),
                 ("test_hold_carries", ctypes.c_int32), ("lane_cols", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("tile_kind", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Profile(ctypes.Structure):
@@ -220,8 +220,8 @@ class MaxSquare:
             pass
 
     def set_tuning(self, band_rows: int = 0, packed_path: int = 0,
-                   test_hold_carries: int = 0, lane_cols: int = 0) -> None:
-        t = _Tuning(band_rows, packed_path, test_hold_carries, lane_cols)
+                   test_hold_carries: int = 0, lane_cols: int = 0, tile_kind: int = 0) -> None:
+        t = _Tuning(band_rows, packed_path, test_hold_carries, lane_cols, tile_kind)
         _check(lib().ms_set_tuning(self._h, ctypes.byref(t)), "ms_set_tuning")
 
     def profile_start(self, max_launches: int = 1 << 20) -> None:
@@ -246,13 +246,13 @@ class MaxSquare:
         _check(lib().ms_autotune(self._h, descs, len(mats), out.data_ptr(), _stream_ptr(stream),
                                  ctypes.byref(t)), "ms_autotune")
         return {"band_rows": t.band_rows, "packed_path": t.packed_path,
-                "lane_cols": t.lane_cols}
+                "lane_cols": t.lane_cols, "tile_kind": t.tile_kind}
 
     def get_tuning(self) -> dict:
         t = _Tuning()
         _check(lib().ms_get_tuning(self._h, ctypes.byref(t)), "ms_get_tuning")
         return {"band_rows": t.band_rows, "packed_path": t.packed_path,
-                "lane_cols": t.lane_cols}
+                "lane_cols": t.lane_cols, "tile_kind": t.tile_kind}
 
     def max_square(self, x, n: int | None = None, fmt: int | None = None, out=None, stream=None):
         import torch

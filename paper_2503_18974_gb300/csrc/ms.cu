@@ -10,6 +10,7 @@
 #include <new>
 #include <vector>
 
+#include "ms_bitile.cuh"
 #include "ms_bits.cuh"
 #include "ms_kernels.cuh"
 
@@ -237,7 +238,8 @@ uint64_t tune_class(const ms_matrix* ins, int64_t count, bool batch) {
 // ms_set_tuning wins, else a
 // cached autotune result for the class, else the context's tuning (automatic).
 ms_tuning effective_tuning(const ms_ctx* ctx, const ms_matrix* ins, int64_t count, bool batch) {
-  if (ctx->tuning.band_rows > 0 || ctx->tuning.lane_cols > 0 || ctx->tuned.empty())
+  if (ctx->tuning.band_rows > 0 || ctx->tuning.lane_cols > 0 || ctx->tuning.tile_kind > 0 ||
+      ctx->tuned.empty())
     return ctx->tuning;
   auto it = ctx->tuned.find(tune_class(ins, count, batch));
   return it == ctx->tuned.end() ? ctx->tuning : it->second;
@@ -259,7 +261,28 @@ ms_status check_matrix(const ms_matrix* in) {
   return MS_OK;
 }
 
-Job plan_job(const ms_tuning& tune, const ms_matrix* in, bool dp, int max_P, int sms) {
+// Band height of bitplane tiles: one tile per warp, so as many tiles as the
+// GPU holds warps at once (two 8-warp blocks per SM), in multiples of 32
+// rows.
+int bit_band_rows(int64_t m, int64_t strips, int sms) {
+  const int64_t slots = 16 * (int64_t)std::max(sms, 1);
+  int64_t br = (m * strips + slots - 1) / slots;
+  br = std::max<int64_t>(32, std::min<int64_t>(16384, (br + 31) / 32 * 32));
+  return (int)std::min<int64_t>(br, std::max<int64_t>(m, 1));
+}
+
+// Single size-only calls on at least this many cells use bitplane tiles when
+// the tuning leaves the choice open (an explicit lane width asks for the dp
+// recurrence).
+constexpr int64_t kBitTilesMinCells = (int64_t)1 << 22;
+bool use_bit_tiles(const ms_tuning& t, const ms_matrix* in) {
+  if (t.tile_kind != 0) return t.tile_kind == 2;
+  if (t.lane_cols > 0) return false;
+  return in->m * in->n >= kBitTilesMinCells;
+}
+
+Job plan_job(const ms_tuning& tune, const ms_matrix* in, bool dp, int max_P, int sms,
+             bool bit_tiles = false) {
   Job j;
   std::memset(&j, 0, sizeof(j));
   j.data = in->data;
@@ -267,10 +290,12 @@ Job plan_job(const ms_tuning& tune, const ms_matrix* in, bool dp, int max_P, int
   j.n = in->n;
   j.ld = in->ld;
   j.fmt = in->fmt;
-  j.P = choose_P(in->m, in->n, dp, tune.lane_cols, max_P, sms);
+  j.P = bit_tiles ? 32 : choose_P(in->m, in->n, dp, tune.lane_cols, max_P, sms);
+  j.tile_kind = bit_tiles ? 1 : 0;
   if (in->m > 0 && in->n > 0) {
     j.strips = (int32_t)strips_for(in->n, j.P);
     j.band_rows = tune.band_rows > 0 ? (int32_t)std::min<int64_t>(tune.band_rows, in->m)
+                  : bit_tiles        ? bit_band_rows(in->m, j.strips, sms)
                                      : auto_band_rows(in->m, j.strips);
     j.bands = (int32_t)((in->m + j.band_rows - 1) / j.band_rows);
   }
@@ -402,7 +427,16 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   const int fuse = ntiles > 0 && ((!DPMAP && j.bits_scratch && j.m * j.n < kFusedFinishCells) ||
                                    (DPMAP && !j.test_hold && j.m * j.n < kFusedFinishCellsDp))
                        ? 1 : 0;
-  if (ntiles > 0) {
+  if (ntiles > 0 && !DPMAP && j.tile_kind == 1) {
+    // bitplane tiles: one tile per warp
+    ProfScope ps(ctx, s, kProfTile);
+    const int wpb = (int)std::min<int64_t>(ms::bt::kWarps, (ntiles + ctx->sms - 1) / ctx->sms);
+    const unsigned grid = (unsigned)((ntiles + wpb - 1) / wpb);
+    const size_t sm = (size_t)wpb * ms::bt::kWarpBytes;
+    if (allow_smem((const void*)ms::k_bitiles_one<FMT>, sm) != cudaSuccess)
+      return cudaGetLastError();
+    ms::k_bitiles_one<FMT><<<grid, 32 * wpb, sm, s>>>(j, ntiles, fuse);
+  } else if (ntiles > 0) {
     ProfScope ps(ctx, s, kProfTile);
     const int64_t warps = (ntiles + 1) / 2;
     // small launches spread their warps over all SMs (one block per SM at
@@ -654,7 +688,8 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   DeviceGuard g(ctx->device);
   const ms_tuning tune = effective_tuning(ctx, in, 1, false);
   if (!dp && !co && bits_search_applies(tune, in)) return run_bits_search(ctx, in, out_dev, s);
-  Job j = plan_job(tune, in, dp != nullptr, 32, ctx->sms);
+  Job j = plan_job(tune, in, dp != nullptr, 32, ctx->sms,
+                   !dp && !co && use_bit_tiles(tune, in));
   st = ensure_workspace(ctx, 1, ms::carry_words(j.m, j.strips_fix), j.strips_fix, s);
   if (st != MS_OK) return st;
   const int64_t bw = bitfix_words(j);
@@ -794,6 +829,7 @@ ms_status ms_set_tuning(ms_ctx* ctx, const ms_tuning* t) {
   if (t->lane_cols != 0 && t->lane_cols != 1 && t->lane_cols != 2 && t->lane_cols != 4 &&
       t->lane_cols != 8 && t->lane_cols != 16 && t->lane_cols != 32)
     return MS_ERR_INVALID;
+  if (t->tile_kind < 0 || t->tile_kind > 2) return MS_ERR_INVALID;
   ctx->tuning = *t;
   return MS_OK;
 }

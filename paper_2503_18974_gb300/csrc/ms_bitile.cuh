@@ -1,0 +1,338 @@
+// Size-only tile pass by bitplanes: the largest square side and its witness
+// of every tile from the corner bitmaps S_t (Sec. 3 of the method restated
+// on bits), 32 cells per 32-bit word.
+//
+// S_t(i, c) = 1 iff the t x t square with bottom-right corner (i, c) is all
+// ones (dp(i, c) >= t, Eq. 1), S_1 = the input.  Four t-squares with the
+// corners of a (t+s)-square cover it when s < t, so
+//   S_{t+s}(i, c) = U(i, c) & U(i - s, c),  U(i, c) = S_t(i, c) & S_t(i, c - s),
+// which gives S_2, S_4, ..., S_32 by doubling (s = t) and any S_{P+s} from
+// S_P (P a power of two, s < P).
+//
+// A warp takes one tile of the dp-recurrence tile pass's geometry (1024
+// window columns, of which the first 32 are halo unless the strip is the
+// matrix's first; `band_rows` counted rows below a 32-row halo).  Lane l owns
+// window word l (columns wc0 + 32l ... + 31) and walks the window's rows top
+// to bottom.  Per row it packs its 32 cells into a word (bytes: four
+// multiplies move 8 cells' 0/1 bytes side by side; packed input: the word
+// itself), derives S_2 ... S_32 of the row from the same-row neighbour word
+// (one shuffle per level) and the level's rows above (a ring per level in
+// shared memory, as deep as the level's largest vertical shift), and stores
+// the row's levels in the rings.
+//
+// Largest side, tile by tile (the method's threshold idea: a tile's best so
+// far, K, only ever grows, and a row matters only if it holds a (K+1)-square
+// corner): every counted row tests S_{K+1} and raises K while the test holds;
+// the first row where K reaches its final value holds the tile's first
+// K-corner in row-major order.  Inside the window S_t is exact for every
+// counted cell while t <= kHalo + 1 (a (kHalo+1)-square ending on a counted
+// cell lies inside the window), so K stops at kHalo + 1: from then on the
+// rows holding S_{kHalo+1} cells are flagged into the matrix's box for the
+// exact fix-up, as in the dp-recurrence tile pass.
+#pragma once
+#include "ms_kernels.cuh"
+
+namespace ms {
+namespace bt {
+
+constexpr int kWarps = 8;                     // warps per block (at most)
+constexpr int kRowWords = 33;                 // ring row: word 0 = 0 (left of lane 0), j+1 = lane j
+constexpr int kRingRows = 63;                 // levels 1, 2, 4, 8, 16, 32: as many rows each
+constexpr int kRingWords = kRingRows * kRowWords;
+constexpr int kInBytes = 4096;                // input ring per warp
+constexpr int kWarpBytes = kInBytes + ((kRingWords * 4 + 15) / 16) * 16;
+constexpr int kTop = kHalo + 1;               // largest exact level (33)
+static_assert(kHalo == 32, "level rings cover shifts up to 32 rows");
+
+template <int FMT>
+struct InGeom {
+  static constexpr int kLane = FMT == MS_U8 ? 32 : 4;  // bytes per lane and row
+  static constexpr int kSlot = 32 * kLane;
+  static constexpr int kDepth = kInBytes / kSlot;       // rows in flight
+  static_assert((kDepth & (kDepth - 1)) == 0 && kDepth >= 4, "input ring depth");
+};
+
+// Streams one lane's 32 window columns down the tile into its ring slots
+// (cp.async for whole aligned chunks, byte loads with zero fill at a ragged
+// or unaligned edge, nothing beyond the matrix's last column).
+template <int FMT>
+struct Reader {
+  using G = InGeom<FMT>;
+  const uint8_t* ptr;
+  const uint8_t* safe;
+  int64_t stride;
+  int row, nrows, mode, nvalid;
+  uint32_t dst;
+
+  __device__ __forceinline__ void init(const Tile& g, int lane, uint32_t ring) {
+    const int64_t col = g.wc0 + 32 * (int64_t)lane;
+    row = 0;
+    nrows = g.nrows;
+    dst = ring + lane * G::kLane;
+    safe = g.base;
+    if constexpr (FMT == MS_U8) {
+      stride = g.ld;
+      ptr = g.base + g.wr0 * g.ld + col;
+      const int64_t valid = g.n - col;
+      nvalid = (int)(valid < 32 ? (valid < 0 ? 0 : valid) : 32);
+      mode = nvalid == 0 ? 0 : ((nvalid == 32 && g.aligned) ? 1 : 2);
+    } else {
+      stride = g.ld * 4;
+      ptr = g.base + (g.wr0 * g.ld + (col >> 5)) * 4;
+      nvalid = 4;
+      mode = col < g.n ? 1 : 0;
+    }
+    const uint32_t zero[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int k = 0; k < G::kDepth; ++k) st_shared_chunk<G::kLane>(dst + k * G::kSlot, zero);
+  }
+
+  // window row `row` into `slot`, then advance
+  __device__ __forceinline__ void issue(int slot) {
+    const bool ok = (unsigned)row < (unsigned)nrows;
+    const uint32_t d = dst + slot * G::kSlot;
+    if (mode == 1) {
+      const uint8_t* src = ok ? ptr : safe;
+      if constexpr (FMT == MS_U8) {
+        cp_async(d, src, 16, ok ? 16 : 0);
+        cp_async(d + 16, src + 16, 16, ok ? 16 : 0);
+      } else {
+        cp_async(d, src, 4, ok ? 4 : 0);
+      }
+    } else if (FMT == MS_U8 && mode == 2) {
+      uint32_t w[8];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) w[b] = 0u;
+      if (ok)
+        for (int b = 0; b < nvalid; ++b) w[b >> 2] |= (uint32_t)__ldg(ptr + b) << (8 * (b & 3));
+      st_shared_chunk<32>(d, w);
+    }
+    ptr += stride;
+    ++row;
+  }
+};
+
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t r;
+  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+  return r;
+}
+
+// 32 cells given as 0/1 bytes (r[k] = columns 4k..4k+3, byte i = column
+// 4k+i) into one word (bit b = column b).  Per 8 columns: q = r[2m] +
+// 16 r[2m+1] holds column 8m+i in bit 8i and column 8m+4+i in bit 8i+4;
+// times 0x00204081 (= 2^21 + 2^14 + 2^7 + 1) the product's bits 21..28 are
+// columns 8m..8m+7 in order (every partial product lands on its own bit, so
+// nothing carries), and a high or low multiply-add moves them to bit 8m.
+// The multiplies issue on the FMA pipe.
+__device__ __forceinline__ uint32_t pack01(const uint32_t r[8]) {
+  uint32_t out = 0u;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const uint32_t q = mad_lo(r[2 * m + 1], 16u, r[2 * m]);
+    const uint32_t y = imul(q, 0x00204081u) & 0x1FE00000u;
+    out = m < 3 ? mad_hi(y, 1u << (8 * m + 11), out) : mad_lo(y, 8u, out);
+  }
+  return out;
+}
+
+// Shared-memory word address of ring row `slot` of level 2^p, lane word `w`
+// (w = lane + 1 for the lane's own word, lane for its left neighbour's).
+__device__ __forceinline__ uint32_t ring_at(uint32_t ring, int p, int slot, int w) {
+  return ring + 4u * (uint32_t)((((1 << p) - 1) + slot) * kRowWords + w);
+}
+__device__ __forceinline__ uint32_t lds(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+// The lane's word of S_t on window row ir (t <= 33): U(ir) & U(ir - s) from
+// ring level P = 2^p <= t, s = t - P (rows above the window read as zeros:
+// their ring slots are not yet written).
+__device__ __forceinline__ uint32_t level_word(uint32_t ring, int lane, int ir, int t) {
+  const int p = 31 - __clz(t);
+  const int P = 1 << p, s = t - P;
+  const int k0 = ir & (P - 1), k1 = (ir - s) & (P - 1);
+  const uint32_t a0 = lds(ring_at(ring, p, k0, lane + 1)), l0 = lds(ring_at(ring, p, k0, lane));
+  const uint32_t a1 = lds(ring_at(ring, p, k1, lane + 1)), l1 = lds(ring_at(ring, p, k1, lane));
+  return a0 & __funnelshift_l(l0, a0, s) & a1 & __funnelshift_l(l1, a1, s);
+}
+
+struct TileOut {
+  unsigned long long key;  // (K, first K-corner) key, 0 if the tile holds no one
+  int r0, r1, c0, c1;      // box of the cells of S_33 (r1 <= r0: none)
+  bool redo;               // B01 pass saw a byte above 1
+};
+
+// One tile by one warp.  B01 (bytes only): the bytes are taken to be 0 or 1;
+// `redo` reports that some byte was not, and the tile must run again.
+template <int FMT, bool B01>
+__device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uint32_t ring) {
+  using G = InGeom<FMT>;
+  const int lane = threadIdx.x & 31;
+  // rows above the window are zeros: clear the level rings
+  for (int k = lane; k < kRingWords; k += 32) sts(ring + 4u * k, 0u);
+  Reader<FMT> rd;
+  rd.init(g, lane, in_ring);
+#pragma unroll
+  for (int d = 0; d < G::kDepth; ++d) {
+    rd.issue(d);
+    cp_async_commit();
+  }
+  const int64_t col = g.wc0 + 32 * (int64_t)lane;
+  const LaneCols lc = lane_cols<32>(col, g.n);
+  // counted columns of this lane (the halo word of a later strip counts none)
+  const uint32_t cm = col >= g.c0 ? lc.mask : 0u;
+  const uint32_t lm = lane == 0 ? 0u : 0xffffffffu;  // lane 0's left is outside
+  uint32_t seen = 0u;
+  int K = 0;
+  TileOut o{0ull, 0x7fffffff, -1, 0x7fffffff, -1, false};
+  __syncwarp();
+
+#pragma unroll 1
+  for (int ir = 0; ir < g.nrows; ++ir) {
+    const int d = ir & (G::kDepth - 1);
+    cp_async_wait<G::kDepth - 1>();
+    const uint32_t a = rd.dst + d * G::kSlot;
+    uint32_t x;
+    if constexpr (FMT == MS_U8) {
+      uint32_t r[8];
+      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
+      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                   : "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) : "r"(a + 16) : "memory");
+      if constexpr (B01) {
+        seen |= r[0] | r[1] | r[2] | r[3] | r[4] | r[5] | r[6] | r[7];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r[k] = (nonzero_msb(r[k]) >> 7) & 0x01010101u;
+      }
+      x = pack01(r);
+    } else {
+      x = lds(a) & lc.mask;
+    }
+    // the slot just read receives the row kDepth ahead
+    rd.issue(d);
+    cp_async_commit();
+
+    // doubling: S_2a(ir) from S_a on this row and on row ir - a
+    uint32_t lv[6];
+    lv[0] = x;
+#pragma unroll
+    for (int p = 0; p < 5; ++p) {
+      const int A = 1 << p;
+      const uint32_t cur = lv[p];
+      const uint32_t left = __shfl_up_sync(kFull, cur, 1) & lm;
+      const int k = ir & (A - 1);
+      const uint32_t o0 = lds(ring_at(ring, p, k, lane + 1));
+      const uint32_t ol = lds(ring_at(ring, p, k, lane));
+      lv[p + 1] = cur & __funnelshift_l(left, cur, A) & o0 & __funnelshift_l(ol, o0, A);
+    }
+    __syncwarp();  // every lane has read the slots about to be overwritten
+#pragma unroll
+    for (int p = 0; p < 6; ++p) sts(ring_at(ring, p, ir & ((1 << p) - 1), lane + 1), lv[p]);
+    __syncwarp();  // the row's levels are visible to the whole warp
+
+    if (ir >= g.cnt_ir0) {
+      if (K < kTop) {
+        // a row without a P-corner (P the level below K+1) holds no
+        // (K+1)-corner: skip the full test
+        const int p = 31 - __clz(K + 1);
+        uint32_t sp = lv[0];
+#pragma unroll
+        for (int q = 1; q < 6; ++q) sp = p == q ? lv[q] : sp;
+        if (__any_sync(kFull, (sp & cm) != 0u)) {
+          while (K < kTop) {
+            const uint32_t w = level_word(ring, lane, ir, K + 1) & cm;
+            const unsigned b = __ballot_sync(kFull, w != 0u);
+            if (!b) break;
+            ++K;
+            const int L = __ffs(b) - 1;
+            const uint32_t wl = __shfl_sync(kFull, w, L);
+            const int64_t c = g.wc0 + 32 * (int64_t)L + (__ffs(wl) - 1);
+            o.key = make_key(K, g.wr0 + ir, c, g.n);
+          }
+        }
+      }
+      if (K >= kTop) {
+        const uint32_t w = level_word(ring, lane, ir, kTop) & cm;
+        const unsigned b = __ballot_sync(kFull, w != 0u);
+        if (b) {
+          const int L0 = __ffs(b) - 1, L1 = 31 - __clz(b);
+          if (o.r0 == 0x7fffffff) o.r0 = (int)(g.wr0 + ir);
+          o.r1 = (int)(g.wr0 + ir + 1);
+          o.c0 = min(o.c0, (int)(g.wc0 + 32 * L0));
+          o.c1 = max(o.c1, (int)min(g.wc0 + 32 * (int64_t)(L1 + 1), g.n));
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if constexpr (B01 && FMT == MS_U8) o.redo = __any_sync(kFull, (seen & 0xfefefefeu) != 0u);
+  __syncwarp();
+  return o;
+}
+
+// Warp w of the launch takes tile w.
+template <int FMT>
+__device__ __forceinline__ void tile_warp(const Job& j, int64_t ntiles, int64_t w) {
+  if (w >= ntiles) return;
+  extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
+  const uint32_t base = (uint32_t)__cvta_generic_to_shared(ms_dyn_smem) +
+                        (threadIdx.x >> 5) * (uint32_t)kWarpBytes;
+  const uint32_t in_ring = base, ring = base + kInBytes;
+  const Tile g = tile_of(j, w);
+  TileOut o;
+  if constexpr (FMT == MS_U8) {
+    o = run_tile<FMT, true>(g, in_ring, ring);
+    if (o.redo) o = run_tile<FMT, false>(g, in_ring, ring);
+  } else {
+    o = run_tile<FMT, false>(g, in_ring, ring);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (o.key) atomicMax(&j.st->key, o.key);
+    if (o.r1 >= 0) {
+      atomicMin(&j.st->box[0], o.r0);
+      atomicMax(&j.st->box[1], o.r1);
+      atomicMin(&j.st->box[2], o.c0);
+      atomicMax(&j.st->box[3], o.c1);
+    }
+  }
+}
+
+}  // namespace bt
+
+// Size-only tile pass of one matrix by bitplanes (tile geometry of lane width
+// 32); fuse != 0: the last block also runs the bitplane fix-up of the box and
+// writes the result, from its own shared memory when the box fits.
+template <int FMT>
+__global__ void __launch_bounds__(256, 2) k_bitiles_one(const Job job, int64_t ntiles, int fuse) {
+  const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  bt::tile_warp<FMT>(job, ntiles, w);
+  if (fuse) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // this block's key and box updates before its ticket
+      s_last = atomicAdd(&job.st->done, 1) == (int)gridDim.x - 1;
+      if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (s_last) {
+      extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
+      fixup_bits_job<FMT>(job, reinterpret_cast<uint32_t*>(ms_dyn_smem),
+                          (int64_t)(blockDim.x >> 5) * bt::kWarpBytes / 4, 1, 0, nullptr);
+    }
+  }
+}
+
+}  // namespace ms

@@ -50,7 +50,7 @@ struct Job {
   int32_t* dp;             // optional dp map (device), may be null
   int64_t ld_dp;
   int32_t dp_aligned;      // dp and ld_dp allow 32-byte (2) or 16-byte (1) vector stores
-  int32_t pad;
+  int32_t tile_kind;       // size-only tile pass: 0 dp recurrence, 1 bitplane tiles (P = 32)
   ms_result* out;
   JobState* st;
   uint32_t* carry;         // fix-up strip carries (carry_words(m, strips_fix) words, 16-B aligned)
