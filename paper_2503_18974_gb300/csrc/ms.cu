@@ -261,14 +261,15 @@ ms_status check_matrix(const ms_matrix* in) {
   return MS_OK;
 }
 
-// Band height of bitplane tiles: one tile per warp, so as many tiles as the
-// GPU holds warps at once (two 8-warp blocks per SM), in multiples of 32
-// rows.
+// Band height of bitplane tiles: one tile per warp, and at most as many
+// tiles as the GPU holds warps at once (two 8-warp blocks per SM), so that
+// no tile waits for a second wave; bands as even as the rows allow, and at
+// least the halo's height.
 int bit_band_rows(int64_t m, int64_t strips, int sms) {
   const int64_t slots = 16 * (int64_t)std::max(sms, 1);
-  int64_t br = (m * strips + slots - 1) / slots;
-  br = std::max<int64_t>(32, std::min<int64_t>(16384, (br + 31) / 32 * 32));
-  return (int)std::min<int64_t>(br, std::max<int64_t>(m, 1));
+  const int64_t bands = std::max<int64_t>(1, slots / std::max<int64_t>(strips, 1));
+  const int64_t br = std::max<int64_t>(ms::kHalo, std::min<int64_t>(16384, (m + bands - 1) / bands));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(br, m));
 }
 
 // Single size-only calls on at least this many cells use bitplane tiles when

@@ -16,9 +16,10 @@
 // to bottom.  Per row it packs its 32 cells into a word (bytes: four
 // multiplies move 8 cells' 0/1 bytes side by side; packed input: the word
 // itself), derives S_2 ... S_32 of the row from the same-row neighbour word
-// (one shuffle per level) and the level's rows above (a ring per level in
-// shared memory, as deep as the level's largest vertical shift), and stores
-// the row's levels in the rings.
+// (one shuffle per level) and the level's rows above (registers for levels
+// 1, 2 and 4, else a ring per level in shared memory as deep as the level),
+// and stores the row's levels in the rings, which also serve the threshold
+// tests below.
 //
 // Largest side, tile by tile (the method's threshold idea: a tile's best so
 // far, K, only ever grows, and a row matters only if it holds a (K+1)-square
@@ -44,10 +45,15 @@ constexpr int kWarpBytes = kInBytes + ((kRingWords * 4 + 15) / 16) * 16;
 constexpr int kTop = kHalo + 1;               // largest exact level (33)
 static_assert(kHalo == 32, "level rings cover shifts up to 32 rows");
 
+// A slot holds one window row: bytes as two 512-byte halves (the first and
+// second 16 bytes of every lane's 32, so that both the 16-byte copies and
+// the 16-byte reads of a warp touch each bank once per 8 lanes), packed
+// input as one word per lane.
 template <int FMT>
 struct InGeom {
-  static constexpr int kLane = FMT == MS_U8 ? 32 : 4;  // bytes per lane and row
-  static constexpr int kSlot = 32 * kLane;
+  static constexpr int kLane = FMT == MS_U8 ? 16 : 4;   // bytes per lane and half
+  static constexpr int kHalves = FMT == MS_U8 ? 2 : 1;
+  static constexpr int kSlot = 32 * kLane * kHalves;
   static constexpr int kDepth = kInBytes / kSlot;       // rows in flight
   static_assert((kDepth & (kDepth - 1)) == 0 && kDepth >= 4, "input ring depth");
 };
@@ -82,9 +88,12 @@ struct Reader {
       nvalid = 4;
       mode = col < g.n ? 1 : 0;
     }
-    const uint32_t zero[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    const uint32_t zero[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int k = 0; k < G::kDepth; ++k) st_shared_chunk<G::kLane>(dst + k * G::kSlot, zero);
+    for (int k = 0; k < G::kDepth; ++k)
+#pragma unroll
+      for (int h = 0; h < G::kHalves; ++h)
+        st_shared_chunk<G::kLane>(dst + k * G::kSlot + h * 32 * G::kLane, zero);
   }
 
   // window row `row` into `slot`, then advance
@@ -95,7 +104,7 @@ struct Reader {
       const uint8_t* src = ok ? ptr : safe;
       if constexpr (FMT == MS_U8) {
         cp_async(d, src, 16, ok ? 16 : 0);
-        cp_async(d + 16, src + 16, 16, ok ? 16 : 0);
+        cp_async(d + 512, src + 16, 16, ok ? 16 : 0);
       } else {
         cp_async(d, src, 4, ok ? 4 : 0);
       }
@@ -105,7 +114,8 @@ struct Reader {
       for (int b = 0; b < 8; ++b) w[b] = 0u;
       if (ok)
         for (int b = 0; b < nvalid; ++b) w[b >> 2] |= (uint32_t)__ldg(ptr + b) << (8 * (b & 3));
-      st_shared_chunk<32>(d, w);
+      st_shared_chunk<16>(d, w);
+      st_shared_chunk<16>(d + 512, w + 4);
     }
     ptr += stride;
     ++row;
@@ -194,6 +204,9 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
   const uint32_t cm = col >= g.c0 ? lc.mask : 0u;
   const uint32_t lm = lane == 0 ? 0u : 0xffffffffu;  // lane 0's left is outside
   uint32_t seen = 0u;
+  // G_a(r) = S_a(r) & S_a(r, c - a) of the last a rows for a = 1, 2, 4 (the
+  // deeper levels read their rows above from the rings)
+  uint32_t g1 = 0u, g2[2] = {0u, 0u}, g4[4] = {0u, 0u, 0u, 0u};
   int K = 0;
   TileOut o{0ull, 0x7fffffff, -1, 0x7fffffff, -1, false};
   __syncwarp();
@@ -209,7 +222,7 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
       asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
       asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                   : "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) : "r"(a + 16) : "memory");
+                   : "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) : "r"(a + 512) : "memory");
       if constexpr (B01) {
         seen |= r[0] | r[1] | r[2] | r[3] | r[4] | r[5] | r[6] | r[7];
       } else {
@@ -224,7 +237,7 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
     rd.issue(d);
     cp_async_commit();
 
-    // doubling: S_2a(ir) from S_a on this row and on row ir - a
+    // doubling: S_2a(ir) = G_a(ir) & G_a(ir - a)
     uint32_t lv[6];
     lv[0] = x;
 #pragma unroll
@@ -232,10 +245,26 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
       const int A = 1 << p;
       const uint32_t cur = lv[p];
       const uint32_t left = __shfl_up_sync(kFull, cur, 1) & lm;
-      const int k = ir & (A - 1);
-      const uint32_t o0 = lds(ring_at(ring, p, k, lane + 1));
-      const uint32_t ol = lds(ring_at(ring, p, k, lane));
-      lv[p + 1] = cur & __funnelshift_l(left, cur, A) & o0 & __funnelshift_l(ol, o0, A);
+      const uint32_t gc = cur & __funnelshift_l(left, cur, A);
+      if (p == 0) {
+        lv[1] = gc & g1;
+        g1 = gc;
+      } else if (p == 1) {
+        lv[2] = gc & g2[0];
+        g2[0] = g2[1];
+        g2[1] = gc;
+      } else if (p == 2) {
+        lv[3] = gc & g4[0];
+        g4[0] = g4[1];
+        g4[1] = g4[2];
+        g4[2] = g4[3];
+        g4[3] = gc;
+      } else {
+        const int k = ir & (A - 1);
+        const uint32_t o0 = lds(ring_at(ring, p, k, lane + 1));
+        const uint32_t ol = lds(ring_at(ring, p, k, lane));
+        lv[p + 1] = gc & o0 & __funnelshift_l(ol, o0, A);
+      }
     }
     __syncwarp();  // every lane has read the slots about to be overwritten
 #pragma unroll

@@ -56,7 +56,7 @@ __device__ __forceinline__ Tile tile_of(const Job& j, int64_t t) {
   g.n = j.n;
   const int64_t r0 = (int64_t)band * j.band_rows;
   const int64_t r1 = min(j.m, r0 + j.band_rows);
-  g.wr0 = band == 0 ? 0 : r0 - kHalo;
+  g.wr0 = r0 >= kHalo ? r0 - kHalo : 0;  // (bands under kHalo rows: the window starts at row 0)
   g.nrows = (int32_t)(r1 - g.wr0);
   g.cnt_ir0 = (int32_t)(r0 - g.wr0);
   if (strip == 0) {
