@@ -20,6 +20,7 @@ using ms::JobState;
 struct ms_ctx {
   int device = 0;
   int sms = 1;        // streaming multiprocessors of the device
+  int bit_slots = 0;  // bitplane tile warps resident at once on the device
   size_t budget = 0;  // 0 = unlimited
   size_t held = 0;    // bytes of device workspace currently held
   ms_tuning tuning{};
@@ -262,11 +263,10 @@ ms_status check_matrix(const ms_matrix* in) {
 }
 
 // Band height of bitplane tiles: one tile per warp, and at most as many
-// tiles as the GPU holds warps at once (two 8-warp blocks per SM), so that
-// no tile waits for a second wave; bands as even as the rows allow, and at
-// least the halo's height.
-int bit_band_rows(int64_t m, int64_t strips, int sms) {
-  const int64_t slots = 16 * (int64_t)std::max(sms, 1);
+// tiles as the GPU holds warps at once (`slots`), so that no tile waits for
+// a second wave; bands as even as the rows allow, and at least the halo's
+// height.
+int bit_band_rows(int64_t m, int64_t strips, int slots) {
   const int64_t bands = std::max<int64_t>(1, slots / std::max<int64_t>(strips, 1));
   const int64_t br = std::max<int64_t>(ms::kHalo, std::min<int64_t>(16384, (m + bands - 1) / bands));
   return (int)std::max<int64_t>(1, std::min<int64_t>(br, m));
@@ -282,8 +282,10 @@ bool use_bit_tiles(const ms_tuning& t, const ms_matrix* in) {
   return in->m * in->n >= kBitTilesMinCells;
 }
 
+// bit_slots > 0: bitplane tiles, that many resident tile warps.
 Job plan_job(const ms_tuning& tune, const ms_matrix* in, bool dp, int max_P, int sms,
-             bool bit_tiles = false) {
+             int bit_slots = 0) {
+  const bool bit_tiles = bit_slots > 0;
   Job j;
   std::memset(&j, 0, sizeof(j));
   j.data = in->data;
@@ -296,7 +298,7 @@ Job plan_job(const ms_tuning& tune, const ms_matrix* in, bool dp, int max_P, int
   if (in->m > 0 && in->n > 0) {
     j.strips = (int32_t)strips_for(in->n, j.P);
     j.band_rows = tune.band_rows > 0 ? (int32_t)std::min<int64_t>(tune.band_rows, in->m)
-                  : bit_tiles        ? bit_band_rows(in->m, j.strips, sms)
+                  : bit_tiles        ? bit_band_rows(in->m, j.strips, bit_slots)
                                      : auto_band_rows(in->m, j.strips);
     j.bands = (int32_t)((in->m + j.band_rows - 1) / j.band_rows);
   }
@@ -329,16 +331,16 @@ constexpr int kFixClusterBlocks = 8;  // a single large matrix's fix-up cluster 
 
 
 // Launch configuration of one `team`-block thread-block cluster of 1024
-// threads with no dynamic shared memory; clears the context's team barrier
-// state first (stream-ordered).
+// threads with `smem` bytes of dynamic shared memory each; clears the
+// context's team barrier state first (stream-ordered).
 cudaError_t cluster_config(ms_ctx* ctx, int team, cudaStream_t s, cudaLaunchConfig_t& cfg,
-                           cudaLaunchAttribute& attr) {
+                           cudaLaunchAttribute& attr, size_t smem = 0) {
   const cudaError_t e = cudaMemsetAsync(ctx->d_sync1, 0, sizeof(ms::TeamSync), s);
   if (e != cudaSuccess) return e;
   cfg = cudaLaunchConfig_t{};
   cfg.gridDim = dim3((unsigned)team);
   cfg.blockDim = dim3(1024);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   attr = cudaLaunchAttribute{};
   attr.id = cudaLaunchAttributeClusterDimension;
@@ -476,13 +478,14 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
       const int team = fix_team_size(j.m * j.n, std::min(kFixClusterBlocks, ctx->sms));
       if (team > 1) {
         // one thread-block cluster: the blocks share every pass over planes
-        // in global memory and meet at the hardware cluster barrier
+        // in global memory and meet at the hardware cluster barrier, unless
+        // the box fits one block's shared memory (rank 0 alone)
         cudaLaunchConfig_t cfg;
         cudaLaunchAttribute attr;
-        const cudaError_t e0 = cluster_config(ctx, team, s, cfg, attr);
+        const cudaError_t e0 = cluster_config(ctx, team, s, cfg, attr, sm);
         if (e0 != cudaSuccess) return e0;
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, ms::k_fixup_bits_one<FMT>, j, (int64_t)0,
-                                                 ctx->d_sync1, 1);
+        const cudaError_t e = cudaLaunchKernelEx(&cfg, ms::k_fixup_bits_one<FMT>, j,
+                                                 (int64_t)(sm / 4), ctx->d_sync1, 1);
         if (e != cudaSuccess) return e;
       } else {
         ms::k_fixup_bits_one<FMT><<<1, 1024, sm, s>>>(j, (int64_t)(sm / 4), nullptr, 0);
@@ -690,7 +693,7 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   const ms_tuning tune = effective_tuning(ctx, in, 1, false);
   if (!dp && !co && bits_search_applies(tune, in)) return run_bits_search(ctx, in, out_dev, s);
   Job j = plan_job(tune, in, dp != nullptr, 32, ctx->sms,
-                   !dp && !co && use_bit_tiles(tune, in));
+                   !dp && !co && use_bit_tiles(tune, in) ? ctx->bit_slots : 0);
   st = ensure_workspace(ctx, 1, ms::carry_words(j.m, j.strips_fix), j.strips_fix, s);
   if (st != MS_OK) return st;
   const int64_t bw = bitfix_words(j);
@@ -782,6 +785,22 @@ ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes) {
     return MS_ERR_CUDA;
   }
   ctx->sms = std::max(ctx->sms, 1);
+  {
+    // bitplane tiles: blocks of kWarps warps that fit an SM at once (both
+    // input formats; the smaller count)
+    const size_t sm = (size_t)ms::bt::kWarps * ms::bt::kWarpBytes;
+    int b0 = 0, b1 = 0;
+    if (allow_smem((const void*)ms::k_bitiles_one<MS_U8>, sm) != cudaSuccess ||
+        allow_smem((const void*)ms::k_bitiles_one<MS_BITS32>, sm) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, ms::k_bitiles_one<MS_U8>,
+                                                      32 * ms::bt::kWarps, sm) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, ms::k_bitiles_one<MS_BITS32>,
+                                                      32 * ms::bt::kWarps, sm) != cudaSuccess) {
+      cudaGetLastError();
+      b0 = b1 = 1;
+    }
+    ctx->bit_slots = ctx->sms * ms::bt::kWarps * std::max(1, std::min(b0, b1));
+  }
   if (cudaMalloc(&ctx->d_sync1, sizeof(ms::TeamSync)) != cudaSuccess) {
     cudaGetLastError();
     cudaEventDestroy(ctx->stage_free);

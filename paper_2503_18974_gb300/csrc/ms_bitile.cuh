@@ -38,7 +38,11 @@ namespace bt {
 
 constexpr int kWarps = 8;                     // warps per block (at most)
 constexpr int kRowWords = 33;                 // ring row: word 0 = 0 (left of lane 0), j+1 = lane j
-constexpr int kRingRows = 63;                 // levels 1, 2, 4, 8, 16, 32: as many rows each
+// ring rows of level 2^p: 2^p for p < 5 (the doubling reads row r - 2^p, a
+// threshold test rows down to r - 2^p + 1), 2 for level 32 (tests of S_32
+// and S_33 read rows r and r - 1 only)
+constexpr int kRingRows = 1 + 2 + 4 + 8 + 16 + 2;
+__host__ __device__ constexpr int ring_depth(int p) { return p < 5 ? 1 << p : 2; }
 constexpr int kRingWords = kRingRows * kRowWords;
 constexpr int kInBytes = 4096;                // input ring per warp
 constexpr int kWarpBytes = kInBytes + ((kRingWords * 4 + 15) / 16) * 16;
@@ -151,8 +155,9 @@ __device__ __forceinline__ uint32_t pack01(const uint32_t r[8]) {
   return out;
 }
 
-// Shared-memory word address of ring row `slot` of level 2^p, lane word `w`
-// (w = lane + 1 for the lane's own word, lane for its left neighbour's).
+// Shared-memory word address of ring row `slot` of level 2^p (its rows start
+// at row 2^p - 1), lane word `w` (w = lane + 1 for the lane's own word, lane
+// for its left neighbour's).
 __device__ __forceinline__ uint32_t ring_at(uint32_t ring, int p, int slot, int w) {
   return ring + 4u * (uint32_t)((((1 << p) - 1) + slot) * kRowWords + w);
 }
@@ -171,7 +176,7 @@ __device__ __forceinline__ void sts(uint32_t a, uint32_t v) {
 __device__ __forceinline__ uint32_t level_word(uint32_t ring, int lane, int ir, int t) {
   const int p = 31 - __clz(t);
   const int P = 1 << p, s = t - P;
-  const int k0 = ir & (P - 1), k1 = (ir - s) & (P - 1);
+  const int k0 = ir & (ring_depth(p) - 1), k1 = (ir - s) & (ring_depth(p) - 1);
   const uint32_t a0 = lds(ring_at(ring, p, k0, lane + 1)), l0 = lds(ring_at(ring, p, k0, lane));
   const uint32_t a1 = lds(ring_at(ring, p, k1, lane + 1)), l1 = lds(ring_at(ring, p, k1, lane));
   return a0 & __funnelshift_l(l0, a0, s) & a1 & __funnelshift_l(l1, a1, s);
@@ -211,96 +216,117 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
   TileOut o{0ull, 0x7fffffff, -1, 0x7fffffff, -1, false};
   __syncwarp();
 
+  // rows go in groups of 8 (the last group runs past the window on the
+  // reader's zero rows, untested), so that every ring slot of the levels 1,
+  // 2, 4 and 32, and every slot inside a group's block of the levels 8 and
+  // 16, is a fixed offset
+  const uint32_t own = ring + 4u * (uint32_t)(lane + 1);  // the lane's word of ring row 0
+  const int ngroups = (g.nrows + 7) >> 3;
 #pragma unroll 1
-  for (int ir = 0; ir < g.nrows; ++ir) {
-    const int d = ir & (G::kDepth - 1);
-    cp_async_wait<G::kDepth - 1>();
-    const uint32_t a = rd.dst + d * G::kSlot;
-    uint32_t x;
-    if constexpr (FMT == MS_U8) {
-      uint32_t r[8];
-      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
-      asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                   : "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) : "r"(a + 512) : "memory");
-      if constexpr (B01) {
-        seen |= r[0] | r[1] | r[2] | r[3] | r[4] | r[5] | r[6] | r[7];
+  for (int gi = 0; gi < ngroups; ++gi) {
+    const int ir0 = gi << 3;
+    const uint32_t r8 = own + 4u * (uint32_t)(7 * kRowWords);
+    const uint32_t r16 = own + 4u * (uint32_t)((15 + (ir0 & 8)) * kRowWords);
+    const uint32_t r32 = own + 4u * (uint32_t)(31 * kRowWords);
+    const int dbase = G::kDepth > 8 ? (ir0 & (G::kDepth - 1)) : 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int ir = ir0 + j;
+      const int d = (dbase + j) & (G::kDepth - 1);
+      cp_async_wait<G::kDepth - 1>();
+      const uint32_t a = rd.dst + d * G::kSlot;
+      uint32_t x;
+      if constexpr (FMT == MS_U8) {
+        uint32_t r[8];
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) : "r"(a + 512) : "memory");
+        if constexpr (B01) {
+          seen |= r[0] | r[1] | r[2] | r[3] | r[4] | r[5] | r[6] | r[7];
+        } else {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) r[k] = (nonzero_msb(r[k]) >> 7) & 0x01010101u;
+        }
+        x = pack01(r);
       } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) r[k] = (nonzero_msb(r[k]) >> 7) & 0x01010101u;
+        x = lds(a) & lc.mask;
       }
-      x = pack01(r);
-    } else {
-      x = lds(a) & lc.mask;
-    }
-    // the slot just read receives the row kDepth ahead
-    rd.issue(d);
-    cp_async_commit();
+      // the slot just read receives the row kDepth ahead
+      rd.issue(d);
+      cp_async_commit();
 
-    // doubling: S_2a(ir) = G_a(ir) & G_a(ir - a)
-    uint32_t lv[6];
-    lv[0] = x;
+      // ring slot of this row for level 2^p (as a byte offset from `own`)
+      auto slot = [&](int p) -> uint32_t {
+        return p == 3 ? r8 + 4u * (uint32_t)(j * kRowWords)
+             : p == 4 ? r16 + 4u * (uint32_t)(j * kRowWords)
+             : p == 5 ? r32 + 4u * (uint32_t)((j & 1) * kRowWords)
+                      : own + 4u * (uint32_t)((((1 << p) - 1) + (j & ((1 << p) - 1))) * kRowWords);
+      };
+      // doubling: S_2a(ir) = G_a(ir) & G_a(ir - a)
+      uint32_t lv[6];
+      lv[0] = x;
 #pragma unroll
-    for (int p = 0; p < 5; ++p) {
-      const int A = 1 << p;
-      const uint32_t cur = lv[p];
-      const uint32_t left = __shfl_up_sync(kFull, cur, 1) & lm;
-      const uint32_t gc = cur & __funnelshift_l(left, cur, A);
-      if (p == 0) {
-        lv[1] = gc & g1;
-        g1 = gc;
-      } else if (p == 1) {
-        lv[2] = gc & g2[0];
-        g2[0] = g2[1];
-        g2[1] = gc;
-      } else if (p == 2) {
-        lv[3] = gc & g4[0];
-        g4[0] = g4[1];
-        g4[1] = g4[2];
-        g4[2] = g4[3];
-        g4[3] = gc;
-      } else {
-        const int k = ir & (A - 1);
-        const uint32_t o0 = lds(ring_at(ring, p, k, lane + 1));
-        const uint32_t ol = lds(ring_at(ring, p, k, lane));
-        lv[p + 1] = gc & o0 & __funnelshift_l(ol, o0, A);
-      }
-    }
-    __syncwarp();  // every lane has read the slots about to be overwritten
-#pragma unroll
-    for (int p = 0; p < 6; ++p) sts(ring_at(ring, p, ir & ((1 << p) - 1), lane + 1), lv[p]);
-    __syncwarp();  // the row's levels are visible to the whole warp
-
-    if (ir >= g.cnt_ir0) {
-      if (K < kTop) {
-        // a row without a P-corner (P the level below K+1) holds no
-        // (K+1)-corner: skip the full test
-        const int p = 31 - __clz(K + 1);
-        uint32_t sp = lv[0];
-#pragma unroll
-        for (int q = 1; q < 6; ++q) sp = p == q ? lv[q] : sp;
-        if (__any_sync(kFull, (sp & cm) != 0u)) {
-          while (K < kTop) {
-            const uint32_t w = level_word(ring, lane, ir, K + 1) & cm;
-            const unsigned b = __ballot_sync(kFull, w != 0u);
-            if (!b) break;
-            ++K;
-            const int L = __ffs(b) - 1;
-            const uint32_t wl = __shfl_sync(kFull, w, L);
-            const int64_t c = g.wc0 + 32 * (int64_t)L + (__ffs(wl) - 1);
-            o.key = make_key(K, g.wr0 + ir, c, g.n);
-          }
+      for (int p = 0; p < 5; ++p) {
+        const int A = 1 << p;
+        const uint32_t cur = lv[p];
+        const uint32_t left = __shfl_up_sync(kFull, cur, 1) & lm;
+        const uint32_t gc = cur & __funnelshift_l(left, cur, A);
+        if (p == 0) {
+          lv[1] = gc & g1;
+          g1 = gc;
+        } else if (p == 1) {
+          lv[2] = gc & g2[j & 1];
+          g2[j & 1] = gc;
+        } else if (p == 2) {
+          lv[3] = gc & g4[j & 3];
+          g4[j & 3] = gc;
+        } else {
+          const uint32_t o0 = lds(slot(p)), ol = lds(slot(p) - 4u);
+          lv[p + 1] = gc & o0 & __funnelshift_l(ol, o0, A);
         }
       }
-      if (K >= kTop) {
-        const uint32_t w = level_word(ring, lane, ir, kTop) & cm;
-        const unsigned b = __ballot_sync(kFull, w != 0u);
-        if (b) {
-          const int L0 = __ffs(b) - 1, L1 = 31 - __clz(b);
-          if (o.r0 == 0x7fffffff) o.r0 = (int)(g.wr0 + ir);
-          o.r1 = (int)(g.wr0 + ir + 1);
-          o.c0 = min(o.c0, (int)(g.wc0 + 32 * L0));
-          o.c1 = max(o.c1, (int)min(g.wc0 + 32 * (int64_t)(L1 + 1), g.n));
+      __syncwarp();  // every lane has read the slots about to be overwritten
+#pragma unroll
+      for (int p = 0; p < 6; ++p) sts(slot(p), lv[p]);
+      __syncwarp();  // the row's levels are visible to the whole warp
+
+      if (ir >= g.cnt_ir0 && ir < g.nrows) {
+        if (K < kTop) {
+          // a row without a P-corner (P the level below K+1) holds no
+          // (K+1)-corner: skip the full test
+          uint32_t sp;
+          switch (31 - __clz(K + 1)) {
+            case 0: sp = lv[0]; break;
+            case 1: sp = lv[1]; break;
+            case 2: sp = lv[2]; break;
+            case 3: sp = lv[3]; break;
+            case 4: sp = lv[4]; break;
+            default: sp = lv[5]; break;
+          }
+          if (__any_sync(kFull, (sp & cm) != 0u)) {
+            while (K < kTop) {
+              const uint32_t w = level_word(ring, lane, ir, K + 1) & cm;
+              const unsigned b = __ballot_sync(kFull, w != 0u);
+              if (!b) break;
+              ++K;
+              const int L = __ffs(b) - 1;
+              const uint32_t wl = __shfl_sync(kFull, w, L);
+              const int64_t c = g.wc0 + 32 * (int64_t)L + (__ffs(wl) - 1);
+              o.key = make_key(K, g.wr0 + ir, c, g.n);
+            }
+          }
+        }
+        if (K >= kTop) {
+          const uint32_t w = level_word(ring, lane, ir, kTop) & cm;
+          const unsigned b = __ballot_sync(kFull, w != 0u);
+          if (b) {
+            const int L0 = __ffs(b) - 1, L1 = 31 - __clz(b);
+            if (o.r0 == 0x7fffffff) o.r0 = (int)(g.wr0 + ir);
+            o.r1 = (int)(g.wr0 + ir + 1);
+            o.c0 = min(o.c0, (int)(g.wc0 + 32 * L0));
+            o.c1 = max(o.c1, (int)min(g.wc0 + 32 * (int64_t)(L1 + 1), g.n));
+          }
         }
       }
     }
@@ -344,7 +370,7 @@ __device__ __forceinline__ void tile_warp(const Job& j, int64_t ntiles, int64_t 
 // 32); fuse != 0: the last block also runs the bitplane fix-up of the box and
 // writes the result, from its own shared memory when the box fits.
 template <int FMT>
-__global__ void __launch_bounds__(256, 2) k_bitiles_one(const Job job, int64_t ntiles, int fuse) {
+__global__ void __launch_bounds__(256, 3) k_bitiles_one(const Job job, int64_t ntiles, int fuse) {
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   bt::tile_warp<FMT>(job, ntiles, w);
   if (fuse) {

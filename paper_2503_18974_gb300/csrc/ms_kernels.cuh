@@ -1063,8 +1063,9 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
   const BitGeo g(rlo, rhi, clo, chi);
   const int wlo = g.wlo, whi = g.whi;
   const bool fits = smem && 2 * (int64_t)g.RP * g.Wv + (int64_t)g.R1 * g.W1 <= smem_words;
-  // (a cluster team always works together: its barrier counts every block)
-  const bool alone = !cluster && (fits || !sync || team_size <= 1);
+  // (a cluster's other blocks may leave: rank 0 alone never uses the cluster
+  // barrier)
+  const bool alone = fits || !sync || team_size <= 1;
   if (alone && rank != 0) return;
   Team tm{alone ? 1 : team_size, alone ? 0 : rank, alone ? nullptr : sync, &j.st->status, 0u,
           false, cluster && !alone};
