@@ -49,77 +49,88 @@ constexpr int kWarpBytes = kInBytes + ((kRingWords * 4 + 15) / 16) * 16;
 constexpr int kTop = kHalo + 1;               // largest exact level (33)
 static_assert(kHalo == 32, "level rings cover shifts up to 32 rows");
 
-// A slot holds one window row: bytes as two 512-byte halves (the first and
-// second 16 bytes of every lane's 32, so that both the 16-byte copies and
-// the 16-byte reads of a warp touch each bank once per 8 lanes), packed
-// input as one word per lane.
+// A slot holds one window row in column order: bytes as 64 chunks of 16
+// (chunk c = columns wc0 + 16c ...), packed input as one word per lane.
 template <int FMT>
 struct InGeom {
-  static constexpr int kLane = FMT == MS_U8 ? 16 : 4;   // bytes per lane and half
-  static constexpr int kHalves = FMT == MS_U8 ? 2 : 1;
-  static constexpr int kSlot = 32 * kLane * kHalves;
-  static constexpr int kDepth = kInBytes / kSlot;       // rows in flight
+  static constexpr int kSlot = FMT == MS_U8 ? 1024 : 128;
+  static constexpr int kDepth = kInBytes / kSlot;  // rows in flight
   static_assert((kDepth & (kDepth - 1)) == 0 && kDepth >= 4, "input ring depth");
 };
 
-// Streams one lane's 32 window columns down the tile into its ring slots
-// (cp.async for whole aligned chunks, byte loads with zero fill at a ragged
-// or unaligned edge, nothing beyond the matrix's last column).
+// A ragged or unaligned chunk: its first `nvalid` bytes by byte loads, zeros
+// after them (out of line: only edge lanes take it, and the row loop stays
+// small for the instruction cache).
+static __device__ __noinline__ void fill_chunk(uint32_t d, const uint8_t* p, int nvalid) {
+  uint32_t w[4] = {0u, 0u, 0u, 0u};
+  for (int b = 0; b < nvalid; ++b) w[b >> 2] |= (uint32_t)__ldg(p + b) << (8 * (b & 3));
+  st_shared_chunk<16>(d, w);
+}
+
+// Streams the tile's window rows into the warp's ring.  Bytes: lane l copies
+// chunks l and 32 + l, so that each of the warp's two 16-byte copies reads
+// 512 contiguous bytes and writes them contiguously (cp.async for whole
+// chunks of 16-byte-aligned rows, byte loads with zero fill at a ragged or
+// unaligned edge, nothing beyond the matrix's last column).  Packed: lane l
+// copies word l.
 template <int FMT>
 struct Reader {
   using G = InGeom<FMT>;
-  const uint8_t* ptr;
+  const uint8_t* ptr;   // the lane's first chunk (bytes) or word (packed) of window row `row`
   const uint8_t* safe;
   int64_t stride;
-  int row, nrows, mode, nvalid;
-  uint32_t dst;
+  int row, nrows;
+  int mode[2], nvalid[2];  // per chunk: 0 none, 1 async, 2 byte loads
+  uint32_t dst;            // the lane's first chunk in slot 0
 
   __device__ __forceinline__ void init(const Tile& g, int lane, uint32_t ring) {
-    const int64_t col = g.wc0 + 32 * (int64_t)lane;
     row = 0;
     nrows = g.nrows;
-    dst = ring + lane * G::kLane;
     safe = g.base;
     if constexpr (FMT == MS_U8) {
       stride = g.ld;
-      ptr = g.base + g.wr0 * g.ld + col;
-      const int64_t valid = g.n - col;
-      nvalid = (int)(valid < 32 ? (valid < 0 ? 0 : valid) : 32);
-      mode = nvalid == 0 ? 0 : ((nvalid == 32 && g.aligned) ? 1 : 2);
+      dst = ring + 16 * lane;
+      ptr = g.base + g.wr0 * g.ld + g.wc0 + 16 * lane;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int64_t valid = g.n - (g.wc0 + 16 * (lane + 32 * k));
+        nvalid[k] = (int)(valid < 16 ? (valid < 0 ? 0 : valid) : 16);
+        mode[k] = nvalid[k] == 0 ? 0 : ((nvalid[k] == 16 && g.aligned) ? 1 : 2);
+      }
     } else {
+      const int64_t col = g.wc0 + 32 * (int64_t)lane;
       stride = g.ld * 4;
+      dst = ring + 4 * lane;
       ptr = g.base + (g.wr0 * g.ld + (col >> 5)) * 4;
-      nvalid = 4;
-      mode = col < g.n ? 1 : 0;
+      nvalid[0] = nvalid[1] = 4;
+      mode[0] = col < g.n ? 1 : 0;
+      mode[1] = 0;
     }
     const uint32_t zero[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int k = 0; k < G::kDepth; ++k)
-#pragma unroll
-      for (int h = 0; h < G::kHalves; ++h)
-        st_shared_chunk<G::kLane>(dst + k * G::kSlot + h * 32 * G::kLane, zero);
+    for (int k = 0; k < G::kDepth; ++k) {
+      if constexpr (FMT == MS_U8) {
+        st_shared_chunk<16>(dst + k * G::kSlot, zero);
+        st_shared_chunk<16>(dst + k * G::kSlot + 512, zero);
+      } else {
+        st_shared_chunk<4>(dst + k * G::kSlot, zero);
+      }
+    }
   }
 
   // window row `row` into `slot`, then advance
   __device__ __forceinline__ void issue(int slot) {
     const bool ok = (unsigned)row < (unsigned)nrows;
     const uint32_t d = dst + slot * G::kSlot;
-    if (mode == 1) {
-      const uint8_t* src = ok ? ptr : safe;
-      if constexpr (FMT == MS_U8) {
-        cp_async(d, src, 16, ok ? 16 : 0);
-        cp_async(d + 512, src + 16, 16, ok ? 16 : 0);
-      } else {
-        cp_async(d, src, 4, ok ? 4 : 0);
-      }
-    } else if (FMT == MS_U8 && mode == 2) {
-      uint32_t w[8];
+    if constexpr (FMT == MS_U8) {
 #pragma unroll
-      for (int b = 0; b < 8; ++b) w[b] = 0u;
-      if (ok)
-        for (int b = 0; b < nvalid; ++b) w[b >> 2] |= (uint32_t)__ldg(ptr + b) << (8 * (b & 3));
-      st_shared_chunk<16>(d, w);
-      st_shared_chunk<16>(d + 512, w + 4);
+      for (int k = 0; k < 2; ++k) {
+        const uint8_t* p = ptr + 512 * k;
+        if (mode[k] == 1) cp_async(d + 512 * k, ok ? p : safe, 16, ok ? 16 : 0);
+        else if (mode[k] == 2) fill_chunk(d + 512 * k, p, ok ? nvalid[k] : 0);
+      }
+    } else {
+      if (mode[0] == 1) cp_async(d, ok ? ptr : safe, 4, ok ? 4 : 0);
     }
     ptr += stride;
     ++row;
@@ -208,6 +219,8 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
   // counted columns of this lane (the halo word of a later strip counts none)
   const uint32_t cm = col >= g.c0 ? lc.mask : 0u;
   const uint32_t lm = lane == 0 ? 0u : 0xffffffffu;  // lane 0's left is outside
+  const uint32_t hoff = (lane & 4) ? 16u : 0u;
+  const uint32_t hsel = (lane & 4) ? 0x1032u : 0x3210u;
   uint32_t seen = 0u;
   // G_a(r) = S_a(r) & S_a(r, c - a) of the last a rows for a = 1, 2, 4 (the
   // deeper levels read their rows above from the rings)
@@ -216,41 +229,45 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
   TileOut o{0ull, 0x7fffffff, -1, 0x7fffffff, -1, false};
   __syncwarp();
 
-  // rows go in groups of 8 (the last group runs past the window on the
+  // rows go in groups of 4 (the last group runs past the window on the
   // reader's zero rows, untested), so that every ring slot of the levels 1,
   // 2, 4 and 32, and every slot inside a group's block of the levels 8 and
   // 16, is a fixed offset
   const uint32_t own = ring + 4u * (uint32_t)(lane + 1);  // the lane's word of ring row 0
-  const int ngroups = (g.nrows + 7) >> 3;
+  const int ngroups = (g.nrows + 3) >> 2;
 #pragma unroll 1
   for (int gi = 0; gi < ngroups; ++gi) {
-    const int ir0 = gi << 3;
-    const uint32_t r8 = own + 4u * (uint32_t)(7 * kRowWords);
-    const uint32_t r16 = own + 4u * (uint32_t)((15 + (ir0 & 8)) * kRowWords);
+    const int ir0 = gi << 2;
+    const uint32_t r8 = own + 4u * (uint32_t)((7 + (ir0 & 4)) * kRowWords);
+    const uint32_t r16 = own + 4u * (uint32_t)((15 + (ir0 & 12)) * kRowWords);
     const uint32_t r32 = own + 4u * (uint32_t)(31 * kRowWords);
-    const int dbase = G::kDepth > 8 ? (ir0 & (G::kDepth - 1)) : 0;
+    const int dbase = G::kDepth > 4 ? (ir0 & (G::kDepth - 1)) : 0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
+    for (int j = 0; j < 4; ++j) {
       const int ir = ir0 + j;
       const int d = (dbase + j) & (G::kDepth - 1);
       cp_async_wait<G::kDepth - 1>();
-      const uint32_t a = rd.dst + d * G::kSlot;
       uint32_t x;
       if constexpr (FMT == MS_U8) {
+        // the lane's 32 bytes (chunks 2l and 2l+1); lanes with bit 2 set read
+        // their second 16 bytes first, so that each 16-byte read of the warp
+        // meets every bank once per 8 lanes, and swap the packed halves back
+        const uint32_t a = in_ring + d * G::kSlot + 32u * lane;
         uint32_t r[8];
         asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a) : "memory");
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "r"(a + hoff) : "memory");
         asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                     : "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) : "r"(a + 512) : "memory");
+                     : "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]) : "r"(a + (16u - hoff))
+                     : "memory");
         if constexpr (B01) {
           seen |= r[0] | r[1] | r[2] | r[3] | r[4] | r[5] | r[6] | r[7];
         } else {
 #pragma unroll
           for (int k = 0; k < 8; ++k) r[k] = (nonzero_msb(r[k]) >> 7) & 0x01010101u;
         }
-        x = pack01(r);
+        x = prmt(pack01(r), 0u, hsel);
       } else {
-        x = lds(a) & lc.mask;
+        x = lds(in_ring + d * G::kSlot + 4u * lane) & lc.mask;
       }
       // the slot just read receives the row kDepth ahead
       rd.issue(d);

@@ -50,7 +50,9 @@ def check(ctx, a, pads=(0, 1), what=""):
 
 SHAPES = [(1, 1), (1, 7), (7, 1), (2, 2), (31, 33), (32, 32), (33, 31), (64, 65), (100, 127),
           (129, 128), (255, 257), (300, 512), (257, 513), (70, 992), (40, 993), (33, 1505),
-          (520, 700), (1000, 1100), (97, 2017), (2100, 90)]
+          (520, 700), (1000, 1100), (97, 2017), (2100, 90),
+          # rows of 16-byte multiples: whole 1024-column tile rows arrive by bulk copies
+          (300, 1024), (97, 2048), (520, 2976), (45, 3008)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -70,6 +72,8 @@ def test_every_side_up_to_past_the_exact_limit(ctx, band_rows):
         rng = np.random.default_rng(40 + band_rows)
         for s in range(1, 41):
             m, n = int(rng.integers(s, 400)), int(rng.integers(s, 2500))
+            if s % 2:
+                n = max(16 * ((n + 15) // 16), 1024)  # bulk-copied rows
             a = gen.bernoulli_u8(m, n, 0.15, seed=1000 * s + band_rows)
             r0, c0 = int(rng.integers(0, m - s + 1)), int(rng.integers(0, n - s + 1))
             a[r0:r0 + s, c0:c0 + s] = 1
@@ -142,6 +146,18 @@ def test_bytes_above_one_strides_and_unaligned_bases(ctx):
     assert ctx.max_square(big[:, 5:2105]).cpu().tolist() == [K, r, c, 0]
     w = bits_dev(a, 2100, pad=1, ldw=70)
     assert ctx.max_square(w, n=2100).cpu().tolist() == [K, r, c, 0]
+    # 16-byte rows (bulk copies) with bytes above one, and a 16-byte-aligned
+    # view whose last tile reaches past the matrix (lane copies there)
+    b = (rng.random((400, 3072)) < 0.9).astype(np.uint8)
+    b[10:90, 2000:2080] = 1
+    (K, r, c), _ = oracle.dp(b, want_map=False)
+    vb = b * rng.integers(1, 256, size=b.shape).astype(np.uint8)
+    assert ctx.max_square(to_dev(vb)).cpu().tolist() == [K, r, c, 0]
+    assert ctx.max_square(to_dev(b)).cpu().tolist() == [K, r, c, 0]
+    big = torch.zeros((400, 3104), dtype=torch.uint8, device=DEV)
+    big[:, 16:3040] = to_dev(b[:, :3024])
+    (K, r, c), _ = oracle.dp(b[:, :3024], want_map=False)
+    assert ctx.max_square(big[:, 16:3040]).cpu().tolist() == [K, r, c, 0]
 
 
 def test_large_matrix_automatic_choice(ctx):
