@@ -281,13 +281,14 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
                       : own + 4u * (uint32_t)((((1 << p) - 1) + (j & ((1 << p) - 1))) * kRowWords);
       };
       // doubling: S_2a(ir) = G_a(ir) & G_a(ir - a)
-      uint32_t lv[6];
+      uint32_t lv[6], lf[5];  // levels 1..32 of the lane's word; levels 1..16 of its left neighbour's
       lv[0] = x;
 #pragma unroll
       for (int p = 0; p < 5; ++p) {
         const int A = 1 << p;
         const uint32_t cur = lv[p];
         const uint32_t left = __shfl_up_sync(kFull, cur, 1) & lm;
+        lf[p] = left;
         const uint32_t gc = cur & __funnelshift_l(left, cur, A);
         if (p == 0) {
           lv[1] = gc & g1;
@@ -304,24 +305,34 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
         }
       }
       __syncwarp();  // every lane has read the slots about to be overwritten
+      // levels 1, 2 and 4 serve only tests of S_t with t < 8: once K >= 7
+      // they are never read again
+      if (K < 7) {
+        sts(slot(0), lv[0]);
+        sts(slot(1), lv[1]);
+        sts(slot(2), lv[2]);
+      }
 #pragma unroll
-      for (int p = 0; p < 6; ++p) sts(slot(p), lv[p]);
+      for (int p = 3; p < 6; ++p) sts(slot(p), lv[p]);
       __syncwarp();  // the row's levels are visible to the whole warp
 
       if (ir >= g.cnt_ir0 && ir < g.nrows) {
         if (K < kTop) {
-          // a row without a P-corner (P the level below K+1) holds no
-          // (K+1)-corner: skip the full test
-          uint32_t sp;
-          switch (31 - __clz(K + 1)) {
-            case 0: sp = lv[0]; break;
-            case 1: sp = lv[1]; break;
-            case 2: sp = lv[2]; break;
-            case 3: sp = lv[3]; break;
-            case 4: sp = lv[4]; break;
-            default: sp = lv[5]; break;
+          // S_{K+1} = U(ir) & U(ir - s) with U = S_P & S_P(c - s), P the
+          // level below K+1: a row whose U(ir) is empty holds no
+          // (K+1)-corner (U(ir) from the row's registers; level 32 has no
+          // neighbour word here and always takes the full test)
+          const int t = K + 1, p = 31 - __clz(t), sh = t - (1 << p);
+          uint32_t sp = 0u, sl = 0u;
+          switch (p) {
+            case 0: sp = lv[0]; sl = lf[0]; break;
+            case 1: sp = lv[1]; sl = lf[1]; break;
+            case 2: sp = lv[2]; sl = lf[2]; break;
+            case 3: sp = lv[3]; sl = lf[3]; break;
+            case 4: sp = lv[4]; sl = lf[4]; break;
+            default: sp = 0xffffffffu; sl = 0xffffffffu; break;
           }
-          if (__any_sync(kFull, (sp & cm) != 0u)) {
+          if (__any_sync(kFull, (sp & __funnelshift_l(sl, sp, sh) & cm) != 0u)) {
             while (K < kTop) {
               const uint32_t w = level_word(ring, lane, ir, K + 1) & cm;
               const unsigned b = __ballot_sync(kFull, w != 0u);
