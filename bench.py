@@ -308,7 +308,7 @@ def profile_traffic(kernel_key):
         return None
     m = re.search(r"sources_sha1:\s*([0-9a-f]{40})", text)
     h = hashlib.sha1()
-    for f in ("ms.cu", "ms_kernels.cuh", "ms_device.cuh", "ms_bits.cuh"):
+    for f in ("ms.cu", "ms_kernels.cuh", "ms_device.cuh", "ms_bits.cuh", "ms_bitile.cuh"):
         p = os.path.join(ROOT, "paper_2503_18974_gb300", "csrc", f)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
@@ -471,7 +471,8 @@ def run_ours(args, world, rank, local, pg):
     # packed size-only work: the autotuner below chooses between the tile
     # kernel and the bitplane search unless --packed-path fixes it
     packed_path = args.packed_path if args.packed_path is not None else 0
-    ctx.set_tuning(packed_path=packed_path, band_rows=args.band_rows, lane_cols=args.lane_cols)
+    ctx.set_tuning(packed_path=packed_path, band_rows=args.band_rows, lane_cols=args.lane_cols,
+                   tile_kind=args.tile_kind)
     wl = make_workload(args.workload, device, host=True)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -483,7 +484,8 @@ def run_ours(args, world, rank, local, pg):
     # the plain form: one autotune per workload class (format, log2 cells) on
     # a representative matrix, cached in the context for the plain calls
     plain_tuned = {}
-    if not wl.dpmap and not args.band_rows and not args.lane_cols and args.packed_path is None:
+    if (not wl.dpmap and not args.band_rows and not args.lane_cols and not args.tile_kind
+            and args.packed_path is None):
         classes = {}
         for mt in wl.mats:
             classes.setdefault((mt.fmt, int(math.log2(max(mt.m * mt.n, 1)))), []).append(mt)
@@ -552,7 +554,10 @@ def run_ours(args, world, rank, local, pg):
     else:
         kern_ms, kern_launches, kern_name = prof.tile_ms, prof.tile_launches, \
             ("k_batch_tiles (persistent tile queue)" if batch_headline
-             else "k_tiles_one (tile pass)")
+             else "k_bitiles_one (bitplane tile pass)"
+             if prof.bit_tile_launches == prof.tile_launches
+             else "k_tiles_one (dp-recurrence tile pass)"
+             if prof.bit_tile_launches == 0 else "k_tiles_one + k_bitiles_one (tile passes)")
     if kern_launches and kern_ms > 0:
         alg_bytes = wl.cells * wl.bytes_per_cell * args.steps
         achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
@@ -631,6 +636,7 @@ def run_ours(args, world, rank, local, pg):
                            "packed_path": packed_path,
                            **({"band_rows": args.band_rows} if args.band_rows else {}),
                            **({"lane_cols": args.lane_cols} if args.lane_cols else {}),
+                           **({"tile_kind": args.tile_kind} if args.tile_kind else {}),
                            "timed_path": ("ms_batch, CUDA graph replay" if batch_headline
                                           else "one ms_* call per matrix (plain)")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
@@ -792,6 +798,8 @@ def main():
                          "(default: the autotuner's choice)")
     ap.add_argument("--band-rows", type=int, default=0,
                     help="rows per tile (0: automatic, or autotuned for multi-matrix runs)")
+    ap.add_argument("--tile-kind", type=int, default=0, choices=[0, 1, 2],
+                    help="size-only tile pass: 0 automatic, 1 dp recurrence, 2 bitplane tiles")
     ap.add_argument("--lane-cols", type=int, default=0,
                     help="columns per lane in a tile (0: automatic)")
     args = ap.parse_args()

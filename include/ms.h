@@ -237,7 +237,9 @@ double ms_server_now(void);
  * or 32; a tile is 32 * lane_cols columns wide).  `tile_kind` selects the
  * size-only tile pass of ms_max_square: 1 = the dp recurrence on two tiles
  * per warp (16-bit lanes), 2 = bitplane tiles (one tile of 1024 columns per
- * warp, 32 cells per word, doubling and threshold tests).
+ * warp, 32 cells per word, doubling and threshold tests); automatically
+ * bitplane tiles when the matrix fills the GPU's resident tile warps with
+ * bands of 64 rows or more.
  * 0 for band_rows, lane_cols or tile_kind = choose automatically from the
  * matrix size. */
 typedef struct {
@@ -287,6 +289,7 @@ typedef struct {
   int64_t other_launches;  /* packed-search kernels and helpers */
   double other_ms;
   int64_t untimed_launches;
+  int64_t bit_tile_launches;  /* of the tile-pass kernels: bitplane tiles */
 } ms_profile;
 
 ms_status ms_profile_start(ms_ctx* ctx, int32_t max_launches);

@@ -75,7 +75,7 @@ class Profile(ctypes.Structure):
     _fields_ = [("tile_launches", ctypes.c_int64), ("tile_ms", ctypes.c_double),
                 ("fixup_launches", ctypes.c_int64), ("fixup_ms", ctypes.c_double),
                 ("other_launches", ctypes.c_int64), ("other_ms", ctypes.c_double),
-                ("untimed_launches", ctypes.c_int64)]
+                ("untimed_launches", ctypes.c_int64), ("bit_tile_launches", ctypes.c_int64)]
 
 
 class _Result(ctypes.Structure):

@@ -32,6 +32,8 @@ struct ms_ctx {
   int32_t* d_progress = nullptr;
   int64_t progress_cap = 0;
   uint32_t* d_bitfix = nullptr;  // bitplanes of the size-only fix-up
+  int32_t* d_first33 = nullptr;  // bitplane tiles: first S_33 row per tile
+  int64_t first33_cap = 0;
   int64_t bitfix_cap = 0;        // uint32 words
   ms::TeamSync* d_sync1 = nullptr;  // barrier of a single matrix's fix-up team
 
@@ -72,6 +74,7 @@ struct ms_ctx {
   std::vector<ProfSlot> prof_pool;
   int64_t prof_count[3] = {0, 0, 0};
   int64_t prof_untimed = 0;
+  int64_t prof_bit = 0;  // tile launches that were bitplane tiles
 };
 
 namespace {
@@ -272,14 +275,18 @@ int bit_band_rows(int64_t m, int64_t strips, int slots) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(br, m));
 }
 
-// Single size-only calls on at least this many cells use bitplane tiles when
-// the tuning leaves the choice open (an explicit lane width asks for the dp
-// recurrence).
-constexpr int64_t kBitTilesMinCells = (int64_t)1 << 22;
-bool use_bit_tiles(const ms_tuning& t, const ms_matrix* in) {
+// Single size-only calls use bitplane tiles when the tuning leaves the
+// choice open (an explicit lane width asks for the dp recurrence) and the
+// matrix fills the GPU's resident tile warps with bands of at least 64 rows:
+// a bitplane tile's rows cost few instructions but a long dependency chain,
+// so smaller matrices (short bands, half their rows halo, few warps) are
+// latency-bound and faster on the dp recurrence, which overlaps two tiles.
+bool use_bit_tiles(const ms_tuning& t, const ms_matrix* in, int bit_slots) {
   if (t.tile_kind != 0) return t.tile_kind == 2;
-  if (t.lane_cols > 0) return false;
-  return in->m * in->n >= kBitTilesMinCells;
+  if (t.lane_cols > 0 || in->m <= 0 || in->n <= 0) return false;
+  const int64_t strips = strips_for(in->n, 32);
+  const int64_t bands = std::max<int64_t>(1, bit_slots / strips);
+  return (in->m + bands - 1) / bands >= 64;
 }
 
 // bit_slots > 0: bitplane tiles, that many resident tile warps.
@@ -433,6 +440,7 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   if (ntiles > 0 && !DPMAP && j.tile_kind == 1) {
     // bitplane tiles: one tile per warp
     ProfScope ps(ctx, s, kProfTile);
+    if (ctx->prof_on) ctx->prof_bit++;
     const int wpb = (int)std::min<int64_t>(ms::bt::kWarps, (ntiles + ctx->sms - 1) / ctx->sms);
     const unsigned grid = (unsigned)((ntiles + wpb - 1) / wpb);
     const size_t sm = (size_t)wpb * ms::bt::kWarpBytes;
@@ -693,13 +701,18 @@ ms_status run_single(ms_ctx* ctx, const ms_matrix* in, int32_t* dp, int64_t ld_d
   const ms_tuning tune = effective_tuning(ctx, in, 1, false);
   if (!dp && !co && bits_search_applies(tune, in)) return run_bits_search(ctx, in, out_dev, s);
   Job j = plan_job(tune, in, dp != nullptr, 32, ctx->sms,
-                   !dp && !co && use_bit_tiles(tune, in) ? ctx->bit_slots : 0);
+                   !dp && !co && use_bit_tiles(tune, in, ctx->bit_slots) ? ctx->bit_slots : 0);
   st = ensure_workspace(ctx, 1, ms::carry_words(j.m, j.strips_fix), j.strips_fix, s);
   if (st != MS_OK) return st;
   const int64_t bw = bitfix_words(j);
   if (bw > 0 && bw <= kBitfixCapWords &&
       grow(ctx, ctx->d_bitfix, ctx->bitfix_cap, bw, capturing(s)) == MS_OK)
     j.bits_scratch = ctx->d_bitfix;
+  // bitplane tiles hand their S_33 rows to the bitplane fix-up
+  if (j.tile_kind == 1 && j.bits_scratch &&
+      grow(ctx, ctx->d_first33, ctx->first33_cap, std::max<int64_t>(tiles_of(j), 1),
+           capturing(s)) == MS_OK)
+    j.first33 = ctx->d_first33;
   j.tile0 = 0;
   j.dp = dp;
   j.ld_dp = ld_dp;
@@ -825,6 +838,7 @@ ms_status ms_destroy(ms_ctx* ctx) {
     release(ctx, ctx->d_carry, ctx->carry_cap);
     release(ctx, ctx->d_progress, ctx->progress_cap);
     release(ctx, ctx->d_bitfix, ctx->bitfix_cap);
+    release(ctx, ctx->d_first33, ctx->first33_cap);
     release(ctx, ctx->d_table, ctx->table_cap);
     release(ctx, ctx->d_lvl, ctx->lvl_cap);
     release(ctx, ctx->d_act, ctx->act_cap);
@@ -1170,6 +1184,7 @@ ms_status ms_profile_start(ms_ctx* ctx, int32_t max_launches) {
   ctx->prof_used = 0;
   ctx->prof_count[0] = ctx->prof_count[1] = ctx->prof_count[2] = 0;
   ctx->prof_untimed = 0;
+  ctx->prof_bit = 0;
   return MS_OK;
 }
 
@@ -1192,6 +1207,7 @@ ms_status ms_profile_stop(ms_ctx* ctx, ms_profile* out) {
   out->other_launches = ctx->prof_count[kProfOther];
   out->other_ms = ms_sum[kProfOther];
   out->untimed_launches = ctx->prof_untimed;
+  out->bit_tile_launches = ctx->prof_bit;
   ctx->prof_used = 0;
   return MS_OK;
 }

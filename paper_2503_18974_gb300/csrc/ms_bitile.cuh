@@ -201,8 +201,11 @@ struct TileOut {
 
 // One tile by one warp.  B01 (bytes only): the bytes are taken to be 0 or 1;
 // `redo` reports that some byte was not, and the tile must run again.
+// plane33 (or null): where the rows of S_33 go from the tile's first S_33
+// row on (row stride pw words).
 template <int FMT, bool B01>
-__device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uint32_t ring) {
+__device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uint32_t ring,
+                                            uint32_t* plane33, int64_t pw) {
   using G = InGeom<FMT>;
   const int lane = threadIdx.x & 31;
   // rows above the window are zeros: clear the level rings
@@ -347,6 +350,7 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
         }
         if (K >= kTop) {
           const uint32_t w = level_word(ring, lane, ir, kTop) & cm;
+          if (plane33 && cm) plane33[(g.wr0 + ir) * pw + (g.wc0 >> 5) + lane] = w;
           const unsigned b = __ballot_sync(kFull, w != 0u);
           if (b) {
             const int L0 = __ffs(b) - 1, L1 = 31 - __clz(b);
@@ -374,14 +378,17 @@ __device__ __forceinline__ void tile_warp(const Job& j, int64_t ntiles, int64_t 
                         (threadIdx.x >> 5) * (uint32_t)kWarpBytes;
   const uint32_t in_ring = base, ring = base + kInBytes;
   const Tile g = tile_of(j, w);
+  const int64_t pw = (j.n + 31) / 32;
+  uint32_t* plane33 = j.first33 ? j.bits_scratch + 2 * j.m * (pw + 2) : nullptr;
   TileOut o;
   if constexpr (FMT == MS_U8) {
-    o = run_tile<FMT, true>(g, in_ring, ring);
-    if (o.redo) o = run_tile<FMT, false>(g, in_ring, ring);
+    o = run_tile<FMT, true>(g, in_ring, ring, plane33, pw);
+    if (o.redo) o = run_tile<FMT, false>(g, in_ring, ring, plane33, pw);
   } else {
-    o = run_tile<FMT, false>(g, in_ring, ring);
+    o = run_tile<FMT, false>(g, in_ring, ring, plane33, pw);
   }
   if ((threadIdx.x & 31) == 0) {
+    if (j.first33) j.first33[w] = o.r1 >= 0 ? o.r0 : 0x7fffffff;
     if (o.key) atomicMax(&j.st->key, o.key);
     if (o.r1 >= 0) {
       atomicMin(&j.st->box[0], o.r0);

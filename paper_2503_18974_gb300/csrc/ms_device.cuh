@@ -61,6 +61,11 @@ struct Job {
   int32_t* corners;        // all largest squares: (row, col) pairs, or null
   int64_t corners_cap;     // pairs that fit in corners
   unsigned long long* corners_count;  // corners found (may exceed the capacity)
+  // Bitplane tiles with fix-up scratch: the first row of tile t holding an
+  // S_33 cell (INT_MAX: none); from that row on the tile wrote its rows of
+  // S_33 (counted words) into the third scratch plane (row stride
+  // ceil(n/32) words), which the fix-up starts from.  Null otherwise.
+  int32_t* first33;
 };
 
 // Appends (i, c) to the job's list of largest-square corners.

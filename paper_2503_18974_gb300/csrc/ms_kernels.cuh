@@ -841,50 +841,59 @@ __device__ __forceinline__ void gbox_reset(int* b) {
   b[3] = 0;
 }
 struct PassBox {
-  int (*slot)[4];  // shared [3][4]: row min, row max, word min, word max
+  int (*part)[32][4];  // shared [2][32][4]: per-warp partial boxes, by pass parity
   int k;
   Team* tm;
   __device__ __forceinline__ void begin() const {
-    if (threadIdx.x == 0) {
-      box_reset(slot[(k + 1) % 3]);
-      if (tm->size > 1 && tm->rank == 0) gbox_reset(tm->sync->box[(k + 1) % 3]);
-    }
+    if (threadIdx.x == 0 && tm->size > 1 && tm->rank == 0) gbox_reset(tm->sync->box[(k + 1) % 3]);
   }
-  // all threads of the team; returns [r0, r1) x [w0, w1) (empty: r1 <= r0)
+  // all threads of the team; returns [r0, r1) x [w0, w1) (empty: r1 <= r0).
+  // Each warp posts its partial box and, after one barrier, folds all of
+  // them itself (no shared-memory atomics to serialise on one address).
   __device__ __forceinline__ void end(int rmin, int rmax, int wmin, int wmax, int out[4]) {
-    rmin = __reduce_min_sync(0xffffffffu, rmin);
-    rmax = __reduce_max_sync(0xffffffffu, rmax);
-    wmin = __reduce_min_sync(0xffffffffu, wmin);
-    wmax = __reduce_max_sync(0xffffffffu, wmax);
-    int* b = slot[k % 3];
-    if ((threadIdx.x & 31) == 0 && rmax >= 0) {
-      atomicMin(b + 0, rmin);
-      atomicMax(b + 1, rmax);
-      atomicMin(b + 2, wmin);
-      atomicMax(b + 3, wmax);
-    }
-    if (tm->size > 1) {
-      __syncthreads();
-      int* g = tm->sync->box[k % 3];
-      if (threadIdx.x == 0 && b[1] >= 0) {
-        atomicMax(g + 0, 0x7fffffff - b[0]);
-        atomicMax(g + 1, b[1] + 1);
-        atomicMax(g + 2, 0x7fffffff - b[2]);
-        atomicMax(g + 3, b[3] + 1);
-      }
-      tm->barrier();
-      if (threadIdx.x == 0) {
-        b[0] = 0x7fffffff - *reinterpret_cast<volatile int*>(g + 0);
-        b[1] = *reinterpret_cast<volatile int*>(g + 1) - 1;
-        b[2] = 0x7fffffff - *reinterpret_cast<volatile int*>(g + 2);
-        b[3] = *reinterpret_cast<volatile int*>(g + 3) - 1;
-      }
+    rmin = __reduce_min_sync(kFull, rmin);
+    rmax = __reduce_max_sync(kFull, rmax);
+    wmin = __reduce_min_sync(kFull, wmin);
+    wmax = __reduce_max_sync(kFull, wmax);
+    int(*p)[4] = part[k & 1];
+    const int lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    if (lane == 0) {
+      int* q = p[threadIdx.x >> 5];
+      q[0] = rmin;
+      q[1] = rmax;
+      q[2] = wmin;
+      q[3] = wmax;
     }
     __syncthreads();
-    out[0] = b[0];
-    out[1] = b[1] + 1;
-    out[2] = b[2];
-    out[3] = b[3] + 1;
+    int b0 = 0x7fffffff, b1 = -1, b2 = 0x7fffffff, b3 = -1;
+    if (lane < nw) {
+      b0 = p[lane][0];
+      b1 = p[lane][1];
+      b2 = p[lane][2];
+      b3 = p[lane][3];
+    }
+    b0 = __reduce_min_sync(kFull, b0);
+    b1 = __reduce_max_sync(kFull, b1);
+    b2 = __reduce_min_sync(kFull, b2);
+    b3 = __reduce_max_sync(kFull, b3);
+    if (tm->size > 1) {
+      int* g = tm->sync->box[k % 3];
+      if (threadIdx.x == 0 && b1 >= 0) {
+        atomicMax(g + 0, 0x7fffffff - b0);
+        atomicMax(g + 1, b1 + 1);
+        atomicMax(g + 2, 0x7fffffff - b2);
+        atomicMax(g + 3, b3 + 1);
+      }
+      tm->barrier();
+      b0 = 0x7fffffff - *reinterpret_cast<volatile int*>(g + 0);
+      b1 = *reinterpret_cast<volatile int*>(g + 1) - 1;
+      b2 = 0x7fffffff - *reinterpret_cast<volatile int*>(g + 2);
+      b3 = *reinterpret_cast<volatile int*>(g + 3) - 1;
+    }
+    out[0] = b0;
+    out[1] = b1 + 1;
+    out[2] = b2;
+    out[3] = b3 + 1;
     ++k;
   }
 };
@@ -941,7 +950,14 @@ __device__ __forceinline__ void grow_pass(const Plane& L, Plane& O, int o_r1, in
           emit_corner(*emit, i, 32 * (int64_t)w + (__ffs(b) - 1));
     }
   });
-  if (first && f != ~0ull) atomicMin(first, f);
+  if (first) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(kFull, f, o);
+      f = v < f ? v : f;
+    }
+    if ((threadIdx.x & 31) == 0 && f != ~0ull) atomicMin(first, f);
+  }
   int box[4];
   pb.end(rmin, rmax, wmin, wmax, box);
   O.ar0 = box[0];
@@ -1040,13 +1056,45 @@ __device__ __forceinline__ Plane build_s32(const Job& j, const BitGeo& g, uint32
   return s32;
 }
 
-__device__ __forceinline__ void pass_box_init(int (*s_box)[4]) {
-  if (threadIdx.x == 0) {
-    s_box[0][0] = 0x7fffffff;
-    s_box[0][1] = -1;
-    s_box[0][2] = 0x7fffffff;
-    s_box[0][3] = -1;
-  }
+// S_33 of rows [rlo, rhi) x words [wlo, whi) from the bitplane tiles' rows
+// (job.first33 set): a word counts where its tile had reached its first
+// S_33 row, and is zero elsewhere (every S_33 cell lies in the flagged box,
+// so nothing outside it is needed).  Written to `out` (pitch whi - wlo);
+// returns its plane.
+__device__ __forceinline__ Plane gather_s33(const Job& j, int rlo, int rhi, int wlo, int whi,
+                                            uint32_t* out, PassBox& pb) {
+  const int64_t pw = (j.n + 31) / 32;
+  const uint32_t* raw = j.bits_scratch + 2 * j.m * (pw + 2);
+  const int BW = whi - wlo;
+  // bitplane tiles are 1024 columns wide (lane width 32); later strips count
+  // 1024 - kHalo of them (constant divisors: no division loops per word)
+  constexpr int64_t W = 32 * 32;
+  Plane s{out, rlo, wlo, BW, 0, 0, 0, 0};
+  int rmin = 0x7fffffff, rmax = -1, wmin = 0x7fffffff, wmax = -1;
+  pb.begin();
+  for_cells<8>(*pb.tm, rhi - rlo, BW, [&](int rr, int cc) {
+    const int i = rlo + rr, w = wlo + cc;
+    const int64_t c = 32 * (int64_t)w;
+    const int64_t strip = c < W ? 0 : 1 + (c - W) / (W - kHalo);
+    const int64_t t = (int64_t)(i / j.band_rows) * j.strips + strip;
+    const int f33 = __ldcg(j.first33 + t);
+    const uint32_t rv = __ldcg(raw + (int64_t)i * pw + w);
+    const uint32_t v = f33 <= i ? rv : 0u;
+    out[rr * BW + cc] = v;
+    if (v) {
+      rmin = min(rmin, i);
+      rmax = max(rmax, i);
+      wmin = min(wmin, w);
+      wmax = max(wmax, w);
+    }
+  });
+  int box[4];
+  pb.end(rmin, rmax, wmin, wmax, box);
+  s.ar0 = box[0];
+  s.ar1 = box[1];
+  s.aw0 = box[2];
+  s.aw1 = box[3];
+  return s;
 }
 
 // Size-only, by a team of `team_size` blocks (ranks 0..team_size-1, all
@@ -1059,18 +1107,22 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
                                            uint32_t* smem, int64_t smem_words, int team_size,
                                            int rank, TeamSync* sync, bool cluster = false) {
   __shared__ unsigned long long s_first;
-  __shared__ int s_box[3][4];
+  __shared__ int s_part[2][32][4];
   const BitGeo g(rlo, rhi, clo, chi);
   const int wlo = g.wlo, whi = g.whi;
-  const bool fits = smem && 2 * (int64_t)g.RP * g.Wv + (int64_t)g.R1 * g.W1 <= smem_words;
+  // bitplane tiles hand over S_33 of the box; else S_32 is built from the
+  // input on the box grown by the halo
+  const bool from33 = j.first33 != nullptr;
+  const int64_t box_words = (int64_t)(rhi - rlo) * (whi - wlo);
+  const bool fits = smem && (from33 ? 3 * box_words
+                                    : 2 * (int64_t)g.RP * g.Wv + (int64_t)g.R1 * g.W1) <= smem_words;
   // (a cluster's other blocks may leave: rank 0 alone never uses the cluster
   // barrier)
   const bool alone = fits || !sync || team_size <= 1;
   if (alone && rank != 0) return;
   Team tm{alone ? 1 : team_size, alone ? 0 : rank, alone ? nullptr : sync, &j.st->status, 0u,
           false, cluster && !alone};
-  PassBox pb{s_box, 0, &tm};
-  pass_box_init(s_box);
+  PassBox pb{s_part, 0, &tm};
   if (threadIdx.x == 0) {
     s_first = ~0ull;
     if (!alone && rank == 0) {
@@ -1079,23 +1131,30 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
   }
   unsigned long long* first = alone ? &s_first : &sync->first;
   uint32_t *buf0, *buf1, *buf2;  // V_32 then levels / S_32 on the grown box / input then levels
-  if (fits) {
+  if (fits && from33) {
+    buf1 = smem;
+    buf0 = smem + box_words;
+    buf2 = smem + 2 * box_words;
+  } else if (fits) {
     buf2 = smem;
     buf0 = smem + g.RP * g.Wv;
     buf1 = smem + 2 * g.RP * g.Wv;
   } else {
+    // (from33: the tiles' S_33 rows sit in the third plane, free again once
+    // the box's S_33 is gathered into the second)
     const int64_t cap = j.m * ((j.n + 31) / 32 + 2);
     buf0 = j.bits_scratch;
     buf1 = j.bits_scratch + cap;
     buf2 = j.bits_scratch + 2 * cap;
   }
-  const Plane s32 = build_s32<FMT>(j, g, buf2, buf0, buf1, pb);
-  // 4. doubling from 32 inside the box [rlo, rhi) x [wlo, whi), then binary
-  //    search; level planes alternate between buf0 and buf2
+  const Plane s_a = from33 ? gather_s33(j, rlo, rhi, wlo, whi, buf1, pb)
+                           : build_s32<FMT>(j, g, buf2, buf0, buf1, pb);
+  // 4. doubling from a = 32 (or 33) inside the box [rlo, rhi) x [wlo, whi),
+  //    then binary search; level planes alternate between buf0 and buf2
   const int BW = whi - wlo;
-  Plane cur = s32, nxt{buf0, rlo, wlo, BW, 0, 0, 0, 0};
+  Plane cur = s_a, nxt{buf0, rlo, wlo, BW, 0, 0, 0, 0};
   uint32_t* spare = buf2;
-  int a = 32, lo, hi;
+  int a = from33 ? kHalo + 1 : 32, lo, hi;
   const int kmax = (int)min(j.m, j.n);
   for (;;) {
     if (2 * a > kmax || cur.empty()) {
@@ -1176,12 +1235,11 @@ template <int FMT>
 __device__ __forceinline__ void fixup_dp_levels(const Job& j, int rlo, int rhi, int clo, int chi,
                                                 uint32_t* smem, int64_t smem_words,
                                                 int cluster_size, int rank, TeamSync* sync) {
-  __shared__ int s_box[3][4];
+  __shared__ int s_part[2][32][4];
   const bool cl = cluster_size > 1;
   Team tm{cl ? cluster_size : 1, cl ? rank : 0, cl ? sync : nullptr, &j.st->status, 0u, false,
           cl};
-  PassBox pb{s_box, 0, &tm};
-  pass_box_init(s_box);
+  PassBox pb{s_part, 0, &tm};
   if (cl) smem = nullptr;
   LevelTab* tab = reinterpret_cast<LevelTab*>(j.bits_scratch);
   uint32_t* base = j.bits_scratch + kTabWords;

@@ -161,15 +161,29 @@ def test_bytes_above_one_strides_and_unaligned_bases(ctx):
 
 
 def test_large_matrix_automatic_choice(ctx):
-    """Default tuning on a large matrix (the automatic choice takes bitplane
-    tiles) and the dp-recurrence tiles forced: both match the oracle."""
+    """The automatic choice: bitplane tiles once the matrix fills the GPU's
+    tile warps with bands of 64 rows or more (checked on a 26000 x 8192 matrix
+    with a planted square on zeros, whose answer is known), the dp
+    recurrence below that; both, and the forced kinds, match the oracle."""
     import paper_2503_18974_gb300 as m
     c = m.MaxSquare(0)
     try:
+        big = torch.zeros((26000, 8192), dtype=torch.uint8, device=DEV)
+        big[20000:20150, 5000:5150] = 1
+        big[20100:20200, 7000:7099] = 1
+        c.profile_start()
+        assert c.max_square(big).cpu().tolist() == [150, 20149, 5149, 0]
+        p = c.profile_stop()
+        assert p.tile_launches == 1 and p.bit_tile_launches == 1
+        del big
         a = gen.bernoulli_u8(3000, 5000, 0.9, seed=99)
         a[2000:2100, 100:200] = 1
         (K, r, cc), _ = oracle.dp(a, want_map=False)
         x = to_dev(a)
+        c.profile_start()
+        assert c.max_square(x).cpu().tolist() == [K, r, cc, 0]
+        assert c.profile_stop().bit_tile_launches == 0
+        c.set_tuning(tile_kind=2)
         assert c.max_square(x).cpu().tolist() == [K, r, cc, 0]
         c.set_tuning(tile_kind=1)
         assert c.max_square(x).cpu().tolist() == [K, r, cc, 0]
