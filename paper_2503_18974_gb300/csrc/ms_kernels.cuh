@@ -885,10 +885,19 @@ struct PassBox {
         atomicMax(g + 3, b3 + 1);
       }
       tm->barrier();
-      b0 = 0x7fffffff - *reinterpret_cast<volatile int*>(g + 0);
-      b1 = *reinterpret_cast<volatile int*>(g + 1) - 1;
-      b2 = 0x7fffffff - *reinterpret_cast<volatile int*>(g + 2);
-      b3 = *reinterpret_cast<volatile int*>(g + 3) - 1;
+      // thread 0 reads the team's box (after its acquire) and shares it
+      // through the partials' first row, which every warp has finished with
+      if (threadIdx.x == 0) {
+        p[0][0] = 0x7fffffff - *reinterpret_cast<volatile int*>(g + 0);
+        p[0][1] = *reinterpret_cast<volatile int*>(g + 1) - 1;
+        p[0][2] = 0x7fffffff - *reinterpret_cast<volatile int*>(g + 2);
+        p[0][3] = *reinterpret_cast<volatile int*>(g + 3) - 1;
+      }
+      __syncthreads();
+      b0 = p[0][0];
+      b1 = p[0][1];
+      b2 = p[0][2];
+      b3 = p[0][3];
     }
     out[0] = b0;
     out[1] = b1 + 1;
