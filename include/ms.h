@@ -239,7 +239,8 @@ double ms_server_now(void);
  * per warp (16-bit lanes), 2 = bitplane tiles (one tile of 1024 columns per
  * warp, 32 cells per word, doubling and threshold tests); automatically
  * bitplane tiles when the matrix fills the GPU's resident tile warps with
- * bands of 64 rows or more.
+ * bands of 64 rows or more.  ms_batch takes bitplane tiles only with
+ * tile_kind 2.
  * 0 for band_rows, lane_cols or tile_kind = choose automatically from the
  * matrix size. */
 typedef struct {

@@ -756,8 +756,11 @@ int tile_steps(const Job& j, int64_t t) {
   const int64_t band = t / j.strips;
   const int64_t r0 = band * j.band_rows;
   const int64_t r1 = std::min<int64_t>(j.m, r0 + j.band_rows);
-  return (int)(r1 - (band == 0 ? 0 : r0 - ms::kHalo)) + 31;
+  // window rows, plus the lane skew of the dp recurrence
+  return (int)(r1 - std::max<int64_t>(0, r0 - ms::kHalo)) + (j.tile_kind ? 0 : 31);
 }
+
+
 
 }  // namespace
 
@@ -922,11 +925,23 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   const ms_tuning tune = effective_tuning(ctx, ins_host, count, true);
   std::vector<Job> jobs((size_t)count);
   int64_t carry = 0, progress = 0, work = 0;
+  // batched matrices take bitplane tiles only when the tuning asks for them
+  // (tile_kind 2): inside the persistent launch, whose registers the
+  // dp-recurrence variants size (two blocks of 8 warps per SM), they measured
+  // slower than the dp recurrence's tile pairs (C4: tile pass 0.95 ms
+  // against 0.60 ms), though their fix-up starts from the tiles' S_33
+  const bool bit_all = tune.tile_kind == 2 && tune.lane_cols == 0;
   for (int32_t i = 0; i < count; ++i) {
-    jobs[i] = plan_job(tune, &ins_host[i], false, 16, 0);  // the batch kernel: P <= 16
-    carry += ms::carry_words(jobs[i].m, jobs[i].strips_fix);
-    progress += jobs[i].strips_fix;
-    work += jobs[i].m * (int64_t)jobs[i].strips;
+    jobs[i] = plan_job(tune, &ins_host[i], false, 16, 0);  // dp recurrence: P <= 16
+    Job& j = jobs[i];
+    if (bit_all && j.m > 0 && j.n > 0) {
+      j.P = 32;
+      j.tile_kind = 1;
+      j.strips = (int32_t)strips_for(j.n, 32);
+    }
+    carry += ms::carry_words(j.m, j.strips_fix);
+    progress += j.strips_fix;
+    work += j.m * (int64_t)j.strips;
   }
   // one band height for the whole batch, sized on the batch's total work
   const int64_t br = tune.band_rows > 0 ? tune.band_rows : auto_band_rows_for(work);
@@ -949,6 +964,12 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     bit_need = 0;
   int64_t bit_off = 0;
   bool any_bits = false, any_strip = false;
+  // first S_33 row per bitplane tile (for their fix-up's hand-over)
+  int64_t f33_need = 0, f33_off = 0;
+  for (const Job& j : jobs)
+    if (j.tile_kind == 1) f33_need += tiles_of(j);
+  const bool f33 = f33_need > 0 &&
+                   grow(ctx, ctx->d_first33, ctx->first33_cap, f33_need, cap) == MS_OK;
   for (int32_t i = 0; i < count; ++i) {
     Job& j = jobs[i];
     j.tile0 = 0;
@@ -966,6 +987,11 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     }
     if (j.bits_scratch) any_bits = true; else any_strip = true;
     const int64_t nt = tiles_of(j);
+    j.first33 = nullptr;
+    if (j.tile_kind == 1 && j.bits_scratch && f33) {
+      j.first33 = ctx->d_first33 + f33_off;
+      f33_off += nt;
+    }
     auto& g = groups[j.fmt * 64 + j.P];
     for (int64_t t = 0; t < nt; ++t) g.push_back(TileRef{i, (int32_t)t, tile_steps(j, t)});
   }
@@ -974,12 +1000,14 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   for (auto& g : groups) {
     std::stable_sort(g.begin(), g.end(),
                      [](const TileRef& a, const TileRef& b) { return a.steps > b.steps; });
-    for (size_t k = 0; k < g.size(); k += 2) {
+    // (bitplane tiles, lane width 32, go one per task)
+    const size_t stride = (!g.empty() && jobs[g[0].job].tile_kind == 1) ? 1 : 2;
+    for (size_t k = 0; k < g.size(); k += stride) {
       ms::PairTask t;
       t.job_a = g[k].job;
       t.tile_a = g[k].tile;
-      t.job_b = k + 1 < g.size() ? g[k + 1].job : -1;
-      t.tile_b = k + 1 < g.size() ? g[k + 1].tile : 0;
+      t.job_b = stride == 2 && k + 1 < g.size() ? g[k + 1].job : -1;
+      t.tile_b = stride == 2 && k + 1 < g.size() ? g[k + 1].tile : 0;
       tasks.push_back(t);
       task_steps.push_back(g[k].steps);
     }

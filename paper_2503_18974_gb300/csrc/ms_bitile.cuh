@@ -37,15 +37,18 @@ namespace ms {
 namespace bt {
 
 constexpr int kWarps = 8;                     // warps per block (at most)
-constexpr int kRowWords = 33;                 // ring row: word 0 = 0 (left of lane 0), j+1 = lane j
-// ring rows of level 2^p: 2^p for p < 5 (the doubling reads row r - 2^p, a
-// threshold test rows down to r - 2^p + 1), 2 for level 32 (tests of S_32
-// and S_33 read rows r and r - 1 only)
-constexpr int kRingRows = 1 + 2 + 4 + 8 + 16 + 2;
+constexpr int kRowWords = 32;                 // ring row: word l = lane l
+// ring rows of level 2^p (p >= 1; S_1 needs none: the only test on it, of
+// S_1 itself, reads the row's own word): 2^p for p < 5 (the doubling reads
+// row r - 2^p, a threshold test rows down to r - 2^p + 1), 2 for level 32
+// (tests of S_32 and S_33 read rows r and r - 1 only); level 2^p starts at
+// ring row 2^p - 2.  With the 4 KB input ring a warp takes exactly 8 KB.
+constexpr int kRingRows = 2 + 4 + 8 + 16 + 2;
 __host__ __device__ constexpr int ring_depth(int p) { return p < 5 ? 1 << p : 2; }
 constexpr int kRingWords = kRingRows * kRowWords;
 constexpr int kInBytes = 4096;                // input ring per warp
-constexpr int kWarpBytes = kInBytes + ((kRingWords * 4 + 15) / 16) * 16;
+constexpr int kWarpBytes = kInBytes + kRingWords * 4;
+static_assert(kWarpBytes == 8192, "a bitplane tile warp takes what a dp-recurrence tile warp does");
 constexpr int kTop = kHalo + 1;               // largest exact level (33)
 static_assert(kHalo == 32, "level rings cover shifts up to 32 rows");
 
@@ -170,7 +173,7 @@ __device__ __forceinline__ uint32_t pack01(const uint32_t r[8]) {
 // at row 2^p - 1), lane word `w` (w = lane + 1 for the lane's own word, lane
 // for its left neighbour's).
 __device__ __forceinline__ uint32_t ring_at(uint32_t ring, int p, int slot, int w) {
-  return ring + 4u * (uint32_t)((((1 << p) - 1) + slot) * kRowWords + w);
+  return ring + 4u * (uint32_t)((((1 << p) - 2) + slot) * kRowWords + w);
 }
 __device__ __forceinline__ uint32_t lds(uint32_t a) {
   uint32_t v;
@@ -184,12 +187,16 @@ __device__ __forceinline__ void sts(uint32_t a, uint32_t v) {
 // The lane's word of S_t on window row ir (t <= 33): U(ir) & U(ir - s) from
 // ring level P = 2^p <= t, s = t - P (rows above the window read as zeros:
 // their ring slots are not yet written).
-__device__ __forceinline__ uint32_t level_word(uint32_t ring, int lane, int ir, int t) {
+__device__ __forceinline__ uint32_t level_word(uint32_t ring, int lane, int ir, int t,
+                                               uint32_t s1) {
+  if (t == 1) return s1;  // S_1 of the row: the lane's own word
   const int p = 31 - __clz(t);
   const int P = 1 << p, s = t - P;
   const int k0 = ir & (ring_depth(p) - 1), k1 = (ir - s) & (ring_depth(p) - 1);
-  const uint32_t a0 = lds(ring_at(ring, p, k0, lane + 1)), l0 = lds(ring_at(ring, p, k0, lane));
-  const uint32_t a1 = lds(ring_at(ring, p, k1, lane + 1)), l1 = lds(ring_at(ring, p, k1, lane));
+  const uint32_t a0 = lds(ring_at(ring, p, k0, lane));
+  const uint32_t l0 = lane ? lds(ring_at(ring, p, k0, lane - 1)) : 0u;
+  const uint32_t a1 = lds(ring_at(ring, p, k1, lane));
+  const uint32_t l1 = lane ? lds(ring_at(ring, p, k1, lane - 1)) : 0u;
   return a0 & __funnelshift_l(l0, a0, s) & a1 & __funnelshift_l(l1, a1, s);
 }
 
@@ -236,14 +243,14 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
   // reader's zero rows, untested), so that every ring slot of the levels 1,
   // 2, 4 and 32, and every slot inside a group's block of the levels 8 and
   // 16, is a fixed offset
-  const uint32_t own = ring + 4u * (uint32_t)(lane + 1);  // the lane's word of ring row 0
+  const uint32_t own = ring + 4u * (uint32_t)lane;  // the lane's word of ring row 0
   const int ngroups = (g.nrows + 3) >> 2;
 #pragma unroll 1
   for (int gi = 0; gi < ngroups; ++gi) {
     const int ir0 = gi << 2;
-    const uint32_t r8 = own + 4u * (uint32_t)((7 + (ir0 & 4)) * kRowWords);
-    const uint32_t r16 = own + 4u * (uint32_t)((15 + (ir0 & 12)) * kRowWords);
-    const uint32_t r32 = own + 4u * (uint32_t)(31 * kRowWords);
+    const uint32_t r8 = own + 4u * (uint32_t)((6 + (ir0 & 4)) * kRowWords);
+    const uint32_t r16 = own + 4u * (uint32_t)((14 + (ir0 & 12)) * kRowWords);
+    const uint32_t r32 = own + 4u * (uint32_t)(30 * kRowWords);
     const int dbase = G::kDepth > 4 ? (ir0 & (G::kDepth - 1)) : 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -281,7 +288,7 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
         return p == 3 ? r8 + 4u * (uint32_t)(j * kRowWords)
              : p == 4 ? r16 + 4u * (uint32_t)(j * kRowWords)
              : p == 5 ? r32 + 4u * (uint32_t)((j & 1) * kRowWords)
-                      : own + 4u * (uint32_t)((((1 << p) - 1) + (j & ((1 << p) - 1))) * kRowWords);
+                      : own + 4u * (uint32_t)((((1 << p) - 2) + (j & ((1 << p) - 1))) * kRowWords);
       };
       // doubling: S_2a(ir) = G_a(ir) & G_a(ir - a)
       uint32_t lv[6], lf[5];  // levels 1..32 of the lane's word; levels 1..16 of its left neighbour's
@@ -303,15 +310,14 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
           lv[3] = gc & g4[j & 3];
           g4[j & 3] = gc;
         } else {
-          const uint32_t o0 = lds(slot(p)), ol = lds(slot(p) - 4u);
+          const uint32_t o0 = lds(slot(p)), ol = lane ? lds(slot(p) - 4u) : 0u;
           lv[p + 1] = gc & o0 & __funnelshift_l(ol, o0, A);
         }
       }
       __syncwarp();  // every lane has read the slots about to be overwritten
-      // levels 1, 2 and 4 serve only tests of S_t with t < 8: once K >= 7
-      // they are never read again
+      // levels 2 and 4 serve only tests of S_t with t < 8: once K >= 7 they
+      // are never read again
       if (K < 7) {
-        sts(slot(0), lv[0]);
         sts(slot(1), lv[1]);
         sts(slot(2), lv[2]);
       }
@@ -337,7 +343,7 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
           }
           if (__any_sync(kFull, (sp & __funnelshift_l(sl, sp, sh) & cm) != 0u)) {
             while (K < kTop) {
-              const uint32_t w = level_word(ring, lane, ir, K + 1) & cm;
+              const uint32_t w = level_word(ring, lane, ir, K + 1, lv[0]) & cm;
               const unsigned b = __ballot_sync(kFull, w != 0u);
               if (!b) break;
               ++K;
@@ -349,7 +355,7 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
           }
         }
         if (K >= kTop) {
-          const uint32_t w = level_word(ring, lane, ir, kTop) & cm;
+          const uint32_t w = level_word(ring, lane, ir, kTop, lv[0]) & cm;
           if (plane33 && cm) plane33[(g.wr0 + ir) * pw + (g.wc0 >> 5) + lane] = w;
           const unsigned b = __ballot_sync(kFull, w != 0u);
           if (b) {
@@ -369,15 +375,15 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
   return o;
 }
 
-// Warp w of the launch takes tile w.
+// One tile (number t of job j) by the calling warp, in its 8 KB of the
+// block's dynamic shared memory; publishes the tile's key and box.
 template <int FMT>
-__device__ __forceinline__ void tile_warp(const Job& j, int64_t ntiles, int64_t w) {
-  if (w >= ntiles) return;
+__device__ __forceinline__ void tile_one(const Job& j, int64_t t) {
   extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
   const uint32_t base = (uint32_t)__cvta_generic_to_shared(ms_dyn_smem) +
                         (threadIdx.x >> 5) * (uint32_t)kWarpBytes;
   const uint32_t in_ring = base, ring = base + kInBytes;
-  const Tile g = tile_of(j, w);
+  const Tile g = tile_of(j, t);
   const int64_t pw = (j.n + 31) / 32;
   uint32_t* plane33 = j.first33 ? j.bits_scratch + 2 * j.m * (pw + 2) : nullptr;
   TileOut o;
@@ -388,7 +394,7 @@ __device__ __forceinline__ void tile_warp(const Job& j, int64_t ntiles, int64_t 
     o = run_tile<FMT, false>(g, in_ring, ring, plane33, pw);
   }
   if ((threadIdx.x & 31) == 0) {
-    if (j.first33) j.first33[w] = o.r1 >= 0 ? o.r0 : 0x7fffffff;
+    if (j.first33) j.first33[t] = o.r1 >= 0 ? o.r0 : 0x7fffffff;
     if (o.key) atomicMax(&j.st->key, o.key);
     if (o.r1 >= 0) {
       atomicMin(&j.st->box[0], o.r0);
@@ -407,7 +413,7 @@ __device__ __forceinline__ void tile_warp(const Job& j, int64_t ntiles, int64_t 
 template <int FMT>
 __global__ void __launch_bounds__(256, 3) k_bitiles_one(const Job job, int64_t ntiles, int fuse) {
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  bt::tile_warp<FMT>(job, ntiles, w);
+  if (w < ntiles) bt::tile_one<FMT>(job, w);
   if (fuse) {
     __shared__ int s_last;
     __syncthreads();
@@ -421,6 +427,41 @@ __global__ void __launch_bounds__(256, 3) k_bitiles_one(const Job job, int64_t n
       extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
       fixup_bits_job<FMT>(job, reinterpret_cast<uint32_t*>(ms_dyn_smem),
                           (int64_t)(blockDim.x >> 5) * bt::kWarpBytes / 4, 1, 0, nullptr);
+    }
+  }
+}
+
+// ---- batch: one persistent launch over a queue of tasks -------------------
+//
+// Warps take tasks from an atomic queue until it runs dry: tile pairs of one
+// format and lane width (the dp recurrence, at most 16 columns per lane) or
+// single bitplane tiles (lane width 32, tile_b unused), groups contiguous and
+// longest first.  Both kinds use 8 KB of shared memory per warp.
+static __global__ void __launch_bounds__(256, 2) k_batch_tiles(const Job* __restrict__ jobs,
+                                                        const PairTask* __restrict__ tasks,
+                                                        int ntasks, int* queue) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(queue, 1);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= ntasks) break;
+    const PairTask task = tasks[t];
+    const Job& A = jobs[task.job_a];
+    const int key = A.fmt * 64 + A.P;
+    switch (key) {
+      case MS_U8 * 64 + 1: batch_task<1, MS_U8>(jobs, task); break;
+      case MS_U8 * 64 + 2: batch_task<2, MS_U8>(jobs, task); break;
+      case MS_U8 * 64 + 4: batch_task<4, MS_U8>(jobs, task); break;
+      case MS_U8 * 64 + 8: batch_task<8, MS_U8>(jobs, task); break;
+      case MS_U8 * 64 + 16: batch_task<16, MS_U8>(jobs, task); break;
+      case MS_U8 * 64 + 32: bt::tile_one<MS_U8>(A, task.tile_a); break;
+      case MS_BITS32 * 64 + 1: batch_task<1, MS_BITS32>(jobs, task); break;
+      case MS_BITS32 * 64 + 2: batch_task<2, MS_BITS32>(jobs, task); break;
+      case MS_BITS32 * 64 + 4: batch_task<4, MS_BITS32>(jobs, task); break;
+      case MS_BITS32 * 64 + 8: batch_task<8, MS_BITS32>(jobs, task); break;
+      case MS_BITS32 * 64 + 32: bt::tile_one<MS_BITS32>(A, task.tile_a); break;
+      default: batch_task<16, MS_BITS32>(jobs, task); break;
     }
   }
 }

@@ -648,37 +648,6 @@ __device__ __forceinline__ void batch_task(const Job* jobs, const PairTask& t) {
   tile_pair<P, FMT, false>(A, ga, B, gb, has_b);
 }
 
-// Warps take tasks (tile pairs of one format and lane width, longest first)
-// from an atomic queue until it runs dry.  Batched matrices use at most 16
-// columns per lane, which keeps this kernel within 128 registers.
-static __global__ void __launch_bounds__(256, 2) k_batch_tiles(const Job* __restrict__ jobs,
-                                                        const PairTask* __restrict__ tasks,
-                                                        int ntasks, int* queue) {
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    int t = 0;
-    if (lane == 0) t = atomicAdd(queue, 1);
-    t = __shfl_sync(kFull, t, 0);
-    if (t >= ntasks) break;
-    const PairTask task = tasks[t];
-    const Job& A = jobs[task.job_a];
-    const int key = A.fmt * 64 + A.P;
-    switch (key) {
-      case MS_U8 * 64 + 1: batch_task<1, MS_U8>(jobs, task); break;
-      case MS_U8 * 64 + 2: batch_task<2, MS_U8>(jobs, task); break;
-      case MS_U8 * 64 + 4: batch_task<4, MS_U8>(jobs, task); break;
-      case MS_U8 * 64 + 8: batch_task<8, MS_U8>(jobs, task); break;
-      case MS_U8 * 64 + 16: batch_task<16, MS_U8>(jobs, task); break;
-      case MS_BITS32 * 64 + 1: batch_task<1, MS_BITS32>(jobs, task); break;
-      case MS_BITS32 * 64 + 2: batch_task<2, MS_BITS32>(jobs, task); break;
-      case MS_BITS32 * 64 + 4: batch_task<4, MS_BITS32>(jobs, task); break;
-      case MS_BITS32 * 64 + 8: batch_task<8, MS_BITS32>(jobs, task); break;
-      default: batch_task<16, MS_BITS32>(jobs, task); break;
-    }
-  }
-}
-
-
 // ---- fix-up and result ------------------------------------------------------
 
 constexpr int kFixWarps = 16;

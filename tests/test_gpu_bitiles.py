@@ -194,3 +194,35 @@ def test_large_matrix_automatic_choice(ctx):
         assert c.max_square(bits_dev(b, 4000, pad=1), n=4000).cpu().tolist() == [K, r, cc, 0]
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("kind,band_rows", [(0, 0), (2, 64), (2, 0)])
+def test_batch_with_bitplane_tiles(ctx, kind, band_rows):
+    """Batches with tile kind 2 run every matrix as bitplane tiles in the
+    persistent launch (kind 0: the dp recurrence's pairs); planted squares
+    below, at and above the exact limit hand their S_33 rows to the batched
+    fix-up.  Every result against the oracle, and alone vs in the mix."""
+    import paper_2503_18974_gb300 as m
+    c = m.MaxSquare(0)
+    try:
+        c.set_tuning(tile_kind=kind, band_rows=band_rows)
+        rng = np.random.default_rng(77 + kind + band_rows)
+        mats, exps = [], []
+        for i in range(24):
+            mm = int(rng.integers(40, 900))
+            nn = int(rng.choice([int(rng.integers(20, 700)), int(rng.integers(768, 3100))]))
+            a = gen.bernoulli_u8(mm, nn, float(rng.choice([0.3, 0.8, 0.93])), seed=900 + i)
+            s = min(mm, nn, int(rng.choice([20, 33, 34, 70, 300])))
+            r0, c0 = int(rng.integers(0, mm - s + 1)), int(rng.integers(0, nn - s + 1))
+            a[r0:r0 + s, c0:c0 + s] = 1
+            (K, r, cc), _ = oracle.dp(a, want_map=False)
+            exps.append([K, r, cc, 0])
+            mats.append((bits_dev(a, nn, pad=1), nn) if i % 3 == 0 else to_dev(a))
+        out = c.batch(mats).cpu().tolist()
+        assert out == exps
+        assert c.batch(mats).cpu().tolist() == exps  # the table reused
+        for i, item in enumerate(mats[:6]):
+            res = c.max_square(*item) if isinstance(item, tuple) else c.max_square(item)
+            assert res.cpu().tolist() == exps[i]
+    finally:
+        c.close()
