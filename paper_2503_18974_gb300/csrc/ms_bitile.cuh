@@ -1,13 +1,14 @@
 // Size-only tile pass by bitplanes: the largest square side and its witness
-// of every tile from the corner bitmaps S_t (Sec. 3 of the method restated
-// on bits), 32 cells per 32-bit word.
+// of every tile from the corner bitmaps S_t (Eq. 1 and the threshold test of
+// Algorithm 1, Sec. 3.2, restated on bits), 32 cells per 32-bit word.
 //
 // S_t(i, c) = 1 iff the t x t square with bottom-right corner (i, c) is all
 // ones (dp(i, c) >= t, Eq. 1), S_1 = the input.  Four t-squares with the
-// corners of a (t+s)-square cover it when s < t, so
+// corners of a (t+s)-square cover it when s <= t, so
 //   S_{t+s}(i, c) = U(i, c) & U(i - s, c),  U(i, c) = S_t(i, c) & S_t(i, c - s),
 // which gives S_2, S_4, ..., S_32 by doubling (s = t) and any S_{P+s} from
-// S_P (P a power of two, s < P).
+// S_P (P a power of two, s < P).  Batches can run these tiles too (one per
+// task of their persistent launch, `k_batch_tiles` below).
 //
 // A warp takes one tile of the dp-recurrence tile pass's geometry (1024
 // window columns, of which the first 32 are halo unless the strip is the
