@@ -332,6 +332,13 @@ def test_invalid_arguments(ctx, ms):
     assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), x.data_ptr(), None) == 6
     desc = ms.describe(x)
     assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), None, None) == 1
+    # tunings out of range are refused and leave the context's tuning as it was
+    before = ctx.get_tuning()
+    for bad in (dict(tile_kind=3), dict(tile_kind=-1), dict(lane_cols=3), dict(band_rows=-1),
+                dict(band_rows=16385), dict(packed_path=2)):
+        with pytest.raises(ms.MSError):
+            ctx.set_tuning(**bad)
+    assert ctx.get_tuning() == before
 
 
 @pytest.fixture
