@@ -337,26 +337,30 @@ constexpr int kFixClusterBlocks = 8;  // a single large matrix's fix-up cluster 
 
 
 
-// Launch configuration of one `team`-block thread-block cluster of 1024
-// threads with `smem` bytes of dynamic shared memory each; clears the
-// context's team barrier state first (stream-ordered).
-cudaError_t cluster_config(ms_ctx* ctx, int team, cudaStream_t s, cudaLaunchConfig_t& cfg,
-                           cudaLaunchAttribute& attr, size_t smem = 0) {
-  const cudaError_t e = cudaMemsetAsync(ctx->d_sync1, 0, sizeof(ms::TeamSync), s);
-  if (e != cudaSuccess) return e;
+// Launch configuration of a fix-up right after its tile pass: `team` blocks
+// of 1024 threads with `smem` bytes of dynamic shared memory each, one
+// thread-block cluster when team > 1, launched as a programmatic dependent
+// of the tile kernel before it on the stream (its blocks wait for that grid
+// with griddepcontrol.wait, so the launch overlaps the tile pass's tail).
+// The context's team barrier state must have been cleared before the tile
+// pass (stream-ordered).
+void fixup_config(int team, size_t smem, cudaStream_t s, cudaLaunchConfig_t& cfg,
+                  cudaLaunchAttribute (&attr)[2]) {
   cfg = cudaLaunchConfig_t{};
   cfg.gridDim = dim3((unsigned)team);
   cfg.blockDim = dim3(1024);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  attr = cudaLaunchAttribute{};
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = (unsigned)team;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
-  cfg.attrs = &attr;
-  cfg.numAttrs = 1;
-  return cudaSuccess;
+  attr[0] = cudaLaunchAttribute{};
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1] = cudaLaunchAttribute{};
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = (unsigned)team;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = team > 1 ? 2 : 1;
 }
 
 ms_status cuda_status(cudaError_t e) { return e == cudaSuccess ? MS_OK : MS_ERR_CUDA; }
@@ -437,6 +441,12 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   const int fuse = ntiles > 0 && ((!DPMAP && j.bits_scratch && j.m * j.n < kFusedFinishCells) ||
                                    (DPMAP && !j.test_hold && j.m * j.n < kFusedFinishCellsDp))
                        ? 1 : 0;
+  // a fix-up cluster after the tile pass: clear its team state now, so that
+  // the fix-up follows the tile kernel directly on the stream
+  const int team = fix_team_size(j.m * j.n, std::min(kFixClusterBlocks, ctx->sms));
+  if (!fuse && team > 1 && j.bits_scratch &&
+      cudaMemsetAsync(ctx->d_sync1, 0, sizeof(ms::TeamSync), s) != cudaSuccess)
+    return cudaGetLastError();
   if (ntiles > 0 && !DPMAP && j.tile_kind == 1) {
     // bitplane tiles: one tile per warp
     ProfScope ps(ctx, s, kProfTile);
@@ -483,21 +493,17 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
       const size_t sm = kBitsFixSmemBytes;
       if (allow_smem((const void*)ms::k_fixup_bits_one<FMT>, sm) != cudaSuccess)
         return cudaGetLastError();
-      const int team = fix_team_size(j.m * j.n, std::min(kFixClusterBlocks, ctx->sms));
-      if (team > 1) {
-        // one thread-block cluster: the blocks share every pass over planes
-        // in global memory and meet at the hardware cluster barrier, unless
-        // the box fits one block's shared memory (rank 0 alone)
-        cudaLaunchConfig_t cfg;
-        cudaLaunchAttribute attr;
-        const cudaError_t e0 = cluster_config(ctx, team, s, cfg, attr, sm);
-        if (e0 != cudaSuccess) return e0;
-        const cudaError_t e = cudaLaunchKernelEx(&cfg, ms::k_fixup_bits_one<FMT>, j,
-                                                 (int64_t)(sm / 4), ctx->d_sync1, 1);
-        if (e != cudaSuccess) return e;
-      } else {
-        ms::k_fixup_bits_one<FMT><<<1, 1024, sm, s>>>(j, (int64_t)(sm / 4), nullptr, 0);
-      }
+      // a team of several blocks is one thread-block cluster: the blocks
+      // share every pass over planes in global memory and meet at the
+      // hardware cluster barrier, unless the box fits one block's shared
+      // memory (rank 0 alone)
+      cudaLaunchConfig_t cfg;
+      cudaLaunchAttribute attr[2];
+      fixup_config(team, sm, s, cfg, attr);
+      const cudaError_t e =
+          cudaLaunchKernelEx(&cfg, ms::k_fixup_bits_one<FMT>, j, (int64_t)(sm / 4),
+                             team > 1 ? ctx->d_sync1 : nullptr, team > 1 ? 1 : 0);
+      if (e != cudaSuccess) return e;
     } else {
       const bool levels = DPMAP && j.bits_scratch && !j.test_hold;
       if (levels) {
@@ -507,19 +513,16 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
         const size_t smb = kBitsFixSmemBytes;
         if (allow_smem((const void*)ms::k_fixup_dp_levels<FMT>, smb) != cudaSuccess)
           return cudaGetLastError();
-        const int team = fix_team_size(j.m * j.n, std::min(kFixClusterBlocks, ctx->sms));
-        if (team > 1) {
-          // a large matrix: one thread-block cluster builds the levels
-          cudaLaunchConfig_t cfg;
-          cudaLaunchAttribute attr;
-          const cudaError_t e0 = cluster_config(ctx, team, s, cfg, attr);
-          if (e0 != cudaSuccess) return e0;
-          const cudaError_t e =
-              cudaLaunchKernelEx(&cfg, ms::k_fixup_dp_levels<FMT>, j, (int64_t)0, ctx->d_sync1);
-          if (e != cudaSuccess) return e;
-        } else {
-          ms::k_fixup_dp_levels<FMT><<<1, 1024, smb, s>>>(j, (int64_t)(smb / 4), nullptr);
-        }
+        // (a large matrix: one thread-block cluster builds the levels, with
+        // its planes in global memory)
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute attr[2];
+        fixup_config(team, team > 1 ? 0 : smb, s, cfg, attr);
+        const cudaError_t e =
+            cudaLaunchKernelEx(&cfg, ms::k_fixup_dp_levels<FMT>, j,
+                               (int64_t)(team > 1 ? 0 : smb / 4),
+                               team > 1 ? ctx->d_sync1 : nullptr);
+        if (e != cudaSuccess) return e;
         ms::k_fixup_dp_cells<<<4 * ctx->sms, 256, 0, s>>>(j);
       }
       const size_t sm = ring_bytes(ms::kFixWarps * 32);

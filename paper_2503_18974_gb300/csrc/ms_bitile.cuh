@@ -413,6 +413,7 @@ __device__ __forceinline__ void tile_one(const Job& j, int64_t t) {
 // writes the result, from its own shared memory when the box fits.
 template <int FMT>
 __global__ void __launch_bounds__(256, 3) k_bitiles_one(const Job job, int64_t ntiles, int fuse) {
+  grid_dependents_may_launch();
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w < ntiles) bt::tile_one<FMT>(job, w);
   if (fuse) {

@@ -560,6 +560,18 @@ __device__ __forceinline__ unsigned long long tile_key(const Best& b, int64_t n)
   return warp_max_u64(make_key(b.val, b.row, b.col, n));
 }
 
+// ---- programmatic dependent launch ------------------------------------------
+// A tile kernel lets the fix-up after it be launched early (its blocks are
+// placed as the tile blocks retire); the fix-up waits, before it reads
+// anything, for the tile grid to finish and its writes to be visible.  Both
+// are no-ops for launches without the programmatic attribute.
+__device__ __forceinline__ void grid_dependents_may_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---- tile pass ------------------------------------------------------------
 
 __device__ __forceinline__ int find_job(const Job* jobs, int njobs, int64_t t) {
@@ -1268,6 +1280,7 @@ template <int FMT>
 __global__ void __launch_bounds__(1024, 1) k_fixup_dp_levels(const Job job, int64_t smem_words,
                                                              TeamSync* sync) {
   extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
+  grid_dependency_wait();
   __shared__ int32_t sbox[4];
   if (threadIdx.x == 0) {
     if (blockIdx.x == 0) reinterpret_cast<LevelTab*>(job.bits_scratch)->n = 0;
@@ -1447,6 +1460,7 @@ template <int FMT>
 __global__ void __launch_bounds__(1024, 1) k_fixup_bits_one(const Job job, int64_t smem_words,
                                                             TeamSync* sync, int cluster) {
   extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
+  grid_dependency_wait();
   fixup_bits_job<FMT>(job, reinterpret_cast<uint32_t*>(ms_dyn_smem), smem_words, (int)gridDim.x,
                       (int)blockIdx.x, sync, cluster != 0);
 }
@@ -1488,6 +1502,7 @@ __global__ void __launch_bounds__(kFixWarps * 32, 1) k_fixup_one(const Job job, 
 // block's warps), then the result -- so that one launch does the whole call.
 template <int P, int FMT, bool DPMAP>
 __global__ void __launch_bounds__(256, 2) k_tiles_one(const Job job, int64_t ntiles, int fuse) {
+  grid_dependents_may_launch();
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   tile_pass_warp<P, FMT, DPMAP>(&job, 1, ntiles, w);
   if (fuse) {
