@@ -21,7 +21,8 @@ _ROOT = os.path.dirname(_HERE)
 LIB_PATH = os.path.join(_HERE, "libms.so")
 _SOURCES = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu", "ms_serve.cu",
                                                       "ms_cube.cu", "ms_kernels.cuh",
-                                                      "ms_device.cuh", "ms_bits.cuh")]
+                                                      "ms_device.cuh", "ms_bits.cuh",
+                                                      "ms_bitile.cuh")]
 _UNITS = [os.path.join(_HERE, "csrc", f) for f in ("ms.cu", "ms_noalloc.cu", "ms_serve.cu",
                                                     "ms_cube.cu")]
 _HEADER = os.path.join(_ROOT, "include", "ms.h")
