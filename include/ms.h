@@ -28,7 +28,8 @@
  * - No C++ exception crosses this interface.  A context is not thread-safe:
  *   use one per host thread (contexts may share a device).
  * - Size limits: m <= 65000 rows and min(m, n) <= 32768; larger inputs
- *   return MS_ERR_UNSUPPORTED.  n itself is limited only by m*n < 2^40.
+ *   return MS_ERR_UNSUPPORTED.  n itself is limited by m*n < 2^40 and
+ *   n < 2^31 - 4096.
  */
 #ifndef MS_H
 #define MS_H

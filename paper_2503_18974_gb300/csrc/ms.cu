@@ -262,6 +262,8 @@ ms_status check_matrix(const ms_matrix* in) {
   if (in->m > 65000) return MS_ERR_UNSUPPORTED;
   if (std::min(in->m, in->n) > 32768) return MS_ERR_UNSUPPORTED;
   if (in->n > ((int64_t)1 << 40) / in->m) return MS_ERR_UNSUPPORTED;
+  // column indices of boxes and tiles are 32-bit
+  if (in->n > ((int64_t)1 << 31) - 4096) return MS_ERR_UNSUPPORTED;
   return MS_OK;
 }
 

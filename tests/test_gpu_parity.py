@@ -330,6 +330,9 @@ def test_invalid_arguments(ctx, ms):
     desc = ms.describe(x)
     desc.m = 70000
     assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), x.data_ptr(), None) == 6
+    desc = ms.describe(x)  # (refused before any access: the buffer is never read)
+    desc.m, desc.n, desc.ld = 1, 1 << 31, 1 << 31
+    assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), x.data_ptr(), None) == 6
     desc = ms.describe(x)
     assert ms.lib().ms_max_square(ctx._h, ms.ctypes.byref(desc), None, None) == 1
     # tunings out of range are refused and leave the context's tuning as it was
