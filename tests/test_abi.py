@@ -69,3 +69,39 @@ def test_python_binding_imports_and_fails_loudly_without_library(tmp_path, monke
     monkeypatch.setattr(ms, "_lib", None)
     with pytest.raises(ImportError):
         ms.lib()
+
+
+def test_binding_structures_match_the_header(tmp_path):
+    """Every structure the binding passes across the C ABI has the header's
+    size and field offsets (compiled from include/ms.h with the host C
+    compiler, so that an edit of one side without the other fails here)."""
+    import shutil
+    import subprocess
+
+    import paper_2503_18974_gb300 as ms
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    pairs = {"ms_matrix": ms._Matrix, "ms_result": ms._Result, "ms_tuning": ms._Tuning,
+             "ms_profile": ms.Profile, "ms_server_config": ms.ServerConfig,
+             "ms_server_completion": ms.Completion, "ms_server_stats": ms.ServerStats,
+             "ms_volume": ms._Volume}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ms.h"', "int main(void) {"]
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "abi"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                           str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        cname, key, val = line.split()
+        got[(cname, key)] = int(val)
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
