@@ -5,26 +5,32 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ou
 Prints ONE JSON line (rank 0).  A step is one pass of the hot path over the
 workload's matrices: the tile pass, the exact fix-up when needed and the
 result write-out, for every matrix.  Inputs are generated in HBM by the
-seeded generator before timing; `value` is cells/s over K device-timed steps
-(max over ranks); `e2e` repeats the measurement with the inputs in pinned
-host memory and the host->device copies and the result read-back inside the
-timed region.  `--impl reference` times the CPU oracle (the paper's
-Algorithm 1, single thread) on the same workload instead.
+seeded generator before timing (larger than L2); `value` is cells/s over K
+device-timed steps (max over ranks); `e2e` repeats the measurement with the
+inputs in pinned host memory and the host->device copies and the result
+read-back inside the timed region.  Every timed result is checked against
+the CPU oracle (the paper's Algorithm 1 on the same matrix, drawn on the
+host).  `--impl reference` times the CPU oracle on a bounded sample of the
+same workload instead.
 
-Workloads (sizes from the configurations this benchmark mirrors):
-  sweep    (default) square uint8 matrices, sides 1000..5000 x densities
-           0.1..0.9 (45 matrices, 495 M cells), one call per matrix; side+witness
-  c1       256 x 256, p = 0.5, seed 0, side + witness + int32 dp map
-  c3-u8 / c3-u8-dp / c3-bits / c3-bits-dp
-           32768 x 32768, p = 0.9, one planted 600-square, seed 3
+Workloads (recipes in gen/configs.py):
+  c3-u8    (default) 32768 x 32768 uint8, p = 0.9, one planted 600-square,
+           seed 3, side + witness: the single large matrix.  The same run
+           reports, under `compare`, the dp-map and packed forms of that
+           matrix and the 4096-matrix batch against plain per-matrix calls.
+  c3-u8-dp / c3-bits / c3-bits-dp   the other forms of that matrix alone
   c3q-*    the same with 8192 rows (for profiler captures)
-  c5       serving stream (see run_serve)
+  c1       256 x 256, p = 0.5, seed 0, side + witness + int32 dp map
+  c2       (alias sweep) square uint8 matrices, sides 1000..5000 x densities
+           0.1..0.9 (45 matrices, 495 M cells), one plain call per matrix
   c4       4096 uint8 matrices, m and n log-uniform in [16, 2048]: one autotuned
-           ms_batch per step replayed from a CUDA graph (plain calls reported beside)
+           ms_batch per step replayed from a CUDA graph (plain calls beside)
+  c5       serving stream of 20 000 requests (see run_serve)
 """
 from __future__ import annotations
 
 import argparse
+import concurrent.futures as cf
 import json
 import math
 import os
@@ -38,39 +44,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Gcells/s on 1 GB300 (% HBM roofline), batched vs plain; serve p50/p99 ms"
+HOST_THREADS = max(1, min(32, os.cpu_count() or 1))
 
 
 # ----------------------------------------------------------------- workloads --
-
-def sweep_specs():
-    specs = []
-    for side in (1000, 2000, 3000, 4000, 5000):
-        for k in range(1, 10):
-            p = k / 10
-            specs.append(dict(m=side, n=side, p=p, seed=10 * (side // 1000) + k, plant=0))
-    return specs
-
-
-def c3_spec():
-    return dict(m=32768, n=32768, p=0.9, seed=3, plant=600)
-
-
-def c4_specs(count=4096):
-    import gen
-    specs = []
-    lo, hi = math.log(16), math.log(2049)
-    for k in range(count):
-        seed = gen.draw(4, k)
-        u = lambda j: (gen.draw(seed, (1 << 40) + j) >> 11) / float(1 << 53)
-        m = min(2048, int(math.exp(lo + (hi - lo) * u(0))))
-        n = min(2048, int(math.exp(lo + (hi - lo) * u(1))))
-        p = (1 + int(9 * u(2))) / 10
-        plant = 0
-        if u(3) < 0.5:
-            plant = 1 + int(min(m, n) * u(4))
-        specs.append(dict(m=m, n=n, p=p, seed=seed, plant=plant))
-    return specs
-
 
 def round_up(x, a):
     return (x + a - 1) // a * a
@@ -106,7 +83,6 @@ class Mat:
             torch.cuda.synchronize()
             self.host = torch.empty(self.dev.shape, dtype=self.dev.dtype, pin_memory=True)
             self.host.copy_(self.dev)
-        self.view = self.dev[:, :n] if fmt == 0 else self.dev
 
     @property
     def nbytes(self):
@@ -116,29 +92,22 @@ class Mat:
         t = self.dev if tensor is None else tensor
         return (t[:, :self.n], None, 0) if self.fmt == 0 else (t, self.n, 1)
 
-
-class Workload:
-    name = ""
-    dtype = "u8"
-    bytes_per_cell = 1.0  # algorithmic bytes of the dominant kernel
-
-    def __init__(self, device):
-        self.device = device
-
-    def config(self):
-        raise NotImplementedError
+    def tune_item(self):
+        return (self.dev, self.n) if self.fmt else self.dev[:, :self.n]
 
 
-class PlainSet(Workload):
-    """A list of matrices, one plain ms_max_square / ms_dp_map call each."""
+class PlainSet:
+    """A list of matrices, one plain ms_max_square / ms_dp_map call each (or
+    one ms_batch over all of them)."""
 
-    def __init__(self, device, specs, fmt=0, dpmap=False, label="", host=False):
-        super().__init__(device)
+    def __init__(self, device, specs, fmt=0, dpmap=False, label="", host=False, batch=False):
         import torch
+        self.device = device
         self.specs = specs
         self.fmt = fmt
         self.dpmap = dpmap
         self.label = label
+        self.batch_headline = batch
         self.mats = [Mat(s, fmt, device, want_host=host) for s in specs]
         self.cells = sum(s["m"] * s["n"] for s in specs)
         self.res = torch.empty((len(specs), 4), dtype=torch.int32, device=device)
@@ -148,9 +117,8 @@ class PlainSet(Workload):
                         for s in specs]
         self.dtype = "u8" if fmt == 0 else "bits32"
         self.bytes_per_cell = (1.0 if fmt == 0 else 0.125) + (4.0 if dpmap else 0.0)
-        self.dev_bufs = None
 
-    def prepare(self, ms, ctx, tensors=None):
+    def prepare(self, ms, tensors=None):
         """ctypes descriptors for every matrix (the C ABI is called directly)."""
         import ctypes
         descs = []
@@ -166,7 +134,6 @@ class PlainSet(Workload):
         return arr, ptrs, res, dps
 
     def step(self, ms, ctx, prep, stream_ptr):
-        """One plain call per matrix."""
         for i in range(len(prep[1])):
             self.step_one(ms, ctx, prep, i, stream_ptr)
 
@@ -185,8 +152,7 @@ class PlainSet(Workload):
 
     def batch_step(self, ms, ctx, prep, stream_ptr):
         """One ms_batch call over all matrices."""
-        arr = prep[0]
-        rc = ms.lib().ms_batch(ctx._h, arr, len(self.mats), self.res.data_ptr(), stream_ptr)
+        rc = ms.lib().ms_batch(ctx._h, prep[0], len(self.mats), self.res.data_ptr(), stream_ptr)
         if rc:
             raise ms.MSError(rc, "ms_batch")
 
@@ -198,32 +164,52 @@ class PlainSet(Workload):
                 "format": self.dtype, "dp_map": self.dpmap,
                 "row_stride": "columns rounded up to 16 bytes" if self.fmt == 0 else
                               "words rounded up to 4",
-                "l2": ("inputs larger than L2 (129 MB)" if self.cells * self.bytes_per_cell
-                       > 129e6 else "L2 flushed between steps")}
+                "l2": ("inputs larger than L2 (129 MB)" if not self.small else
+                       "L2 flushed between steps (a 512 MiB buffer rewritten outside each "
+                       "step's event pair)")}
+
+    @property
+    def small(self):
+        return self.cells * self.bytes_per_cell <= 256e6
+
+
+def workload_specs(name):
+    from gen import configs
+    if name in ("c2", "sweep"):
+        return configs.c2_specs()
+    if name == "c1":
+        return [configs.c1_spec()]
+    if name == "c4":
+        return configs.c4_specs()
+    if name.startswith("c3"):
+        spec = configs.c3_spec()
+        return [dict(spec, m=8192)] if name.startswith("c3q") else [spec]
+    raise SystemExit(f"unknown workload {name}")
 
 
 def make_workload(name, device, host=False):
-    if name == "sweep":
-        return PlainSet(device, sweep_specs(), label="paper-scale sweep: square uint8, sides "
+    specs = workload_specs(name)
+    if name in ("c2", "sweep"):
+        return PlainSet(device, specs, label="paper-scale sweep: square uint8, sides "
                         "1000..5000 x p 0.1..0.9, seed 10*side/1000+10p, side + witness, "
                         "one call per matrix", host=host)
     if name == "c1":
-        return PlainSet(device, [dict(m=256, n=256, p=0.5, seed=0, plant=0)], dpmap=True,
+        return PlainSet(device, specs, dpmap=True,
                         label="256x256 uint8, p=0.5, seed 0, side + witness + int32 dp map",
                         host=host)
     if name.startswith("c3"):
         fmt = 1 if "bits" in name else 0
         dp = name.endswith("-dp")
-        spec = c3_spec()
-        if name.startswith("c3q"):  # a quarter of it (8192 rows) for profiler captures
-            spec = dict(spec, m=8192)
-        return PlainSet(device, [spec], fmt=fmt, dpmap=dp,
-                        label=f"{spec['m']}x32768 {'bit-packed' if fmt else 'uint8'}, p=0.9, "
+        m = specs[0]["m"]
+        return PlainSet(device, specs, fmt=fmt, dpmap=dp,
+                        label=f"{m}x32768 {'bit-packed' if fmt else 'uint8'}, p=0.9, "
                               f"planted 600-square, seed 3, "
-                              f"{'dp map' if dp else 'side + witness'}", host=host)
+                              f"{'dp map' if dp else 'side + witness'}, one plain call",
+                        host=host)
     if name == "c4":
-        return PlainSet(device, c4_specs(), label="batch of 4096 uint8 matrices, m,n "
-                        "log-uniform in [16,2048], p in 0.1..0.9, half planted", host=host)
+        return PlainSet(device, specs, label="batch of 4096 uint8 matrices, m,n "
+                        "log-uniform in [16,2048], p in 0.1..0.9, half planted", host=host,
+                        batch=True)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -269,7 +255,7 @@ class ClockSampler:
             self.proc.wait(timeout=2)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        lo, hi = (self.t0 or 0) - 0.25, (self.t1 or 1e30) + 0.25
+        lo, hi = (self.t0 or 0) - 0.05, (self.t1 or 1e30) + 0.05
         rows = [s for (t, s) in self.samples if lo <= t <= hi] or [s for (_, s) in self.samples]
         mhz, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -288,7 +274,8 @@ class ClockSampler:
         mhz.sort()
         return {"sm_mhz": mhz[len(mhz) // 2] if mhz else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(rows),
-                "window": "timed region +-0.25 s, 200 ms sampling"}
+                "window": "the workload's steps run back to back for about 1 s before and "
+                          "through the timed region, 200 ms sampling"}
 
 
 def measured_peaks():
@@ -349,46 +336,53 @@ def max_over_ranks(pg, x, device):
     return float(t.item())
 
 
+def trimmed_mean(times, trim=0.1):
+    """The paper's protocol (Sec. 4.2): drop the top and bottom 10%."""
+    times = sorted(times)
+    k = int(len(times) * trim)
+    kept = times[k:len(times) - k] if len(times) > 2 * k else times
+    return sum(kept) / len(kept)
+
+
 # ------------------------------------------------------------ CPU (oracle) ----
 
-def cpu_oracle_run(specs, budget_s=20.0, reps=5):
-    """The paper's Algorithm 1 (oracle.freq, one thread) on the workload's
-    matrices regenerated on the host; the paper's protocol scaled down: one
-    warm-up, then repetitions until the budget, 10% trimmed mean."""
-    import numpy as np
-
+def host_matrices(specs, threads=HOST_THREADS):
+    """The workload's matrices drawn on the host (the oracle side's inputs)."""
     import gen
+    if len(specs) == 1:
+        return [gen.config_u8(specs[0], threads=threads)]
+    with cf.ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(gen.config_u8, specs))
+
+
+def oracle_results(mats, threads=HOST_THREADS):
+    """Algorithm 1 (oracle_freq) on every matrix, in host threads."""
     import oracle
-    oracle.build()
-    mats = []
-    tot = 0
-    for s in specs:
-        a = gen.bernoulli_u8(s["m"], s["n"], s["p"], s["seed"])
-        if s["plant"]:
-            r, c = gen.plant_pos(s["seed"], s["m"], s["n"], s["plant"])
-            a[r:r + s["plant"], c:c + s["plant"]] = 1
-        mats.append(a)
-        tot += s["m"] * s["n"]
-    for a in mats:
-        oracle.freq(a)
+    with cf.ThreadPoolExecutor(threads) as ex:
+        return [list(r) for r in ex.map(oracle.freq, mats)]
+
+
+def time_oracle(fn, mats, warmup, reps):
+    for _ in range(warmup):
+        for a in mats:
+            fn(a)
     times = []
-    t_start = time.perf_counter()
-    while len(times) < reps and (time.perf_counter() - t_start) < budget_s:
+    for _ in range(reps):
         t0 = time.perf_counter()
         for a in mats:
-            oracle.freq(a)
+            fn(a)
         times.append(time.perf_counter() - t0)
-    times.sort()
-    trim = int(len(times) * 0.1)
-    kept = times[trim:len(times) - trim] if len(times) > 2 * trim else times
-    sec = sum(kept) / len(kept)
-    t0 = time.perf_counter()
-    oracle.dp_rows(mats[len(mats) // 2])
-    dp_rate = mats[len(mats) // 2].size / (time.perf_counter() - t0)
-    return tot, sec, len(times), dp_rate
+    return trimmed_mean(times)
 
 
-def cpu_sample_specs(specs, max_cells=600_000_000):
+def cpu_sample(specs, name, max_cells):
+    """A bounded sample of the workload for CPU timing: whole matrices up to
+    max_cells, or the first rows of a single larger matrix."""
+    if len(specs) == 1 and specs[0]["m"] * specs[0]["n"] > max_cells:
+        s = specs[0]
+        rows = max(1, max_cells // s["n"])
+        return None, rows, f"rows 0..{rows - 1} of the {s['m']}x{s['n']} matrix " \
+                           f"({rows * s['n'] / 1e6:.0f} M cells)"
     out, tot = [], 0
     for s in specs:
         c = s["m"] * s["n"]
@@ -396,17 +390,58 @@ def cpu_sample_specs(specs, max_cells=600_000_000):
             continue
         out.append(s)
         tot += c
-    return out
+    return out, None, f"{len(out)} of {len(specs)} matrices ({tot / 1e6:.0f} M cells)"
 
 
-def cpu_baseline(specs):
-    sample = cpu_sample_specs(specs)
-    cells, sec, reps, dp_rate = cpu_oracle_run(sample)
-    return {"value": cells / sec / 1e9, "unit": "Gcells/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(sample)} of {len(specs)} matrices ({cells / 1e6:.0f} M cells), "
-                      f"Algorithm 1 (oracle_freq), 1 warm-up + {reps} timed passes, "
-                      f"10% trimmed mean",
-            "oracle_dp_rows_gcells_s": dp_rate / 1e9}
+def sample_matrices(specs, name, max_cells, full=None):
+    sel, rows, desc = cpu_sample(specs, name, max_cells)
+    if sel is None:
+        import numpy as np
+        if full is not None:
+            return [np.ascontiguousarray(full[0][:rows])], desc
+        # the first rows of the matrix: the same cells (cell (i, j) is draw
+        # i*n + j of the matrix's stream) and the part of the planted square
+        # that falls in them
+        import gen
+        s = specs[0]
+        a = gen.bernoulli_u8(rows, s["n"], s["p"], s["seed"], threads=HOST_THREADS)
+        if s["plant"]:
+            r, c = gen.plant_pos(s["seed"], s["m"], s["n"], s["plant"])
+            a[r:min(rows, r + s["plant"]), c:c + s["plant"]] = 1
+        return [a], desc
+    return host_matrices(sel), desc
+
+
+def cpu_baseline(specs, name, full=None, max_cells=134_217_728, warmup=3, reps=10):
+    """The oracle as it stands, one host core, on a bounded sample of the
+    workload, with the paper's protocol (Sec. 4.2-4.3: warm-ups, repeated
+    timed passes, 10% trimmed mean): Algorithm 1, the textbook O(mn) DP and
+    the O(n)-space DP of Sec. 4.9."""
+    import oracle
+    mats, desc = sample_matrices(specs, name, max_cells, full)
+    cells = sum(a.size for a in mats)
+    t_freq = time_oracle(oracle.freq, mats, warmup, reps)
+    t_dp = time_oracle(lambda a: oracle.dp(a, want_map=False), mats, warmup, reps)
+    t_rows = time_oracle(oracle.dp_rows, mats, warmup, reps)
+    return {"value": cells / t_freq / 1e9, "unit": "Gcells/s", "cores": 1, "kind": "oracle",
+            "sample": f"{desc}; Algorithm 1 (oracle_freq), {warmup} warm-up + {reps} timed "
+                      f"passes, 10% trimmed mean, one host thread",
+            "oracle_dp_gcells_s": cells / t_dp / 1e9,
+            "oracle_dp_rows_gcells_s": cells / t_rows / 1e9,
+            "freq_speedup_vs_dp": t_dp / t_freq, "freq_speedup_vs_dp_rows": t_rows / t_freq,
+            "host": host_cpu()}
+
+
+def host_cpu():
+    model = None
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model}
 
 
 # ------------------------------------------------------------------- arms -----
@@ -414,19 +449,10 @@ def cpu_baseline(specs):
 def run_reference(args, world, rank, local, pg):
     if rank != 0:
         return
-    specs = {"sweep": sweep_specs, "c1": lambda: [dict(m=256, n=256, p=0.5, seed=0, plant=0)],
-             "c4": c4_specs}.get(args.workload, lambda: [c3_spec()])()
-    sample = cpu_sample_specs(specs, max_cells=120_000_000)
-    import gen
     import oracle
     oracle.build()
-    mats = []
-    for s in sample:
-        a = gen.bernoulli_u8(s["m"], s["n"], s["p"], s["seed"])
-        if s["plant"]:
-            r, c = gen.plant_pos(s["seed"], s["m"], s["n"], s["plant"])
-            a[r:r + s["plant"], c:c + s["plant"]] = 1
-        mats.append(a)
+    specs = workload_specs(args.workload)
+    mats, desc = sample_matrices(specs, args.workload, 67_108_864)
     cells = sum(a.size for a in mats)
     for _ in range(args.warmup):
         for a in mats:
@@ -441,48 +467,75 @@ def run_reference(args, world, rank, local, pg):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": args.workload, "sample_matrices": len(mats),
-                       "sample_cells": cells},
+            "config": {"workload": args.workload, "sample": desc, "sample_cells": cells},
             "cpu_baseline": {"value": value, "unit": "Gcells/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: {len(mats)} of {len(specs)} matrices "
-                                       f"({cells / 1e6:.0f} M cells) through Algorithm 1"},
+                             "sample": f"each step: {desc} through Algorithm 1 "
+                                       f"(oracle_freq), one host thread"},
             "e2e": {"value": value, "unit": "Gcells/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def timed(fn, steps, stream):
+def timed(fn, steps, stream, flush=None):
+    """Device time of `steps` calls of fn (ms, CUDA events on `stream`).  With
+    `flush` (a buffer larger than L2) every step is timed by its own event
+    pair and the buffer is rewritten between steps, outside the pairs."""
     import torch
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(steps):
+    if flush is None:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for a, b in evs:
+        flush.add_(1)
+        a.record(stream)
         fn()
-    ev1.record(stream)
+        b.record(stream)
     torch.cuda.synchronize()
-    return ev0.elapsed_time(ev1)
+    return sum(a.elapsed_time(b) for a, b in evs)
 
 
-def run_ours(args, world, rank, local, pg):
+def kernel_label(prof, batch):
+    if prof.other_ms > prof.tile_ms:
+        return "k_bits_search (bitplane doubling + binary search)"
+    if batch:
+        return "k_batch_tiles (persistent tile queue)"
+    if prof.bit_tile_launches == prof.tile_launches:
+        return "k_bitiles_one (bitplane tile pass)"
+    if prof.bit_tile_launches == 0:
+        return "k_tiles_one (dp-recurrence tile pass)"
+    return "k_tiles_one + k_bitiles_one (tile passes)"
+
+
+def measure(args, ms, name, device, stream, pg=None, clocks=False, e2e=False, steps=None):
+    """Time one workload in a context of its own: K device-timed steps of its
+    headline form (plain calls, or the graph-replayed batch), the dominant
+    kernel's own time, the other form beside it, and optionally e2e.
+    Returns the measurements and the device results of the last step."""
+    ctx = ms.MaxSquare(device.index or 0)
+    try:
+        return _measure(args, ms, ctx, name, device, stream, pg, clocks, e2e, steps)
+    finally:
+        ctx.close()
+
+
+def _measure(args, ms, ctx, name, device, stream, pg, clocks, e2e, steps):
     import torch
-
-    import paper_2503_18974_gb300 as ms
-    device = torch.device(f"cuda:{local}")
-    torch.cuda.set_device(device)
-    ms.build()
-    ctx = ms.MaxSquare(local)
-    # packed size-only work: the autotuner below chooses between the tile
-    # kernel and the bitplane search unless --packed-path fixes it
-    packed_path = args.packed_path if args.packed_path is not None else 0
-    ctx.set_tuning(packed_path=packed_path, band_rows=args.band_rows, lane_cols=args.lane_cols,
-                   tile_kind=args.tile_kind)
-    wl = make_workload(args.workload, device, host=True)
+    steps = steps or args.steps
+    wl = make_workload(name, device, host=e2e)
     torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
     sp = stream.cuda_stream or None
-    prep = wl.prepare(ms, ctx)
-    batch_headline = args.workload == "c4"
+    prep = wl.prepare(ms)
+    batch_headline = wl.batch_headline
     multi = len(wl.mats) > 1 and not wl.dpmap
+    ctx.set_tuning(packed_path=args.packed_path if args.packed_path is not None else 0,
+                   band_rows=args.band_rows, lane_cols=args.lane_cols, tile_kind=args.tile_kind)
 
     # the plain form: one autotune per workload class (format, log2 cells) on
     # a representative matrix, cached in the context for the plain calls
@@ -494,14 +547,13 @@ def run_ours(args, world, rank, local, pg):
             classes.setdefault((mt.fmt, int(math.log2(max(mt.m * mt.n, 1)))), []).append(mt)
         for key, group in sorted(classes.items()):
             rep = sorted(group, key=lambda mt: mt.m * mt.n)[len(group) // 2]
-            plain_tuned[f"fmt{key[0]}_2^{key[1]}"] = ctx.autotune(
-                [rep.args()[:2] if rep.fmt else rep.args()[0]])
+            plain_tuned[f"fmt{key[0]}_2^{key[1]}"] = ctx.autotune([rep.tune_item()])
 
     # the batched form: autotuned, then captured in a CUDA graph
     graph = None
     tuned = None
     if multi:
-        tuned = ctx.autotune([mt.args()[:2] if mt.fmt else mt.args()[0] for mt in wl.mats])
+        tuned = ctx.autotune([mt.tune_item() for mt in wl.mats])
         wl.batch_step(ms, ctx, prep, sp)  # uploads the job table outside the capture
         torch.cuda.synchronize()
         graph = torch.cuda.CUDAGraph()
@@ -518,32 +570,44 @@ def run_ours(args, world, rank, local, pg):
         graph.replay()
 
     headline = batched if batch_headline else plain
-
-    for _ in range(args.warmup):
+    flush = torch.zeros(128 << 20, dtype=torch.int32, device=device) if wl.small else None
+    for _ in range(max(args.warmup, 3)):
         headline()
     torch.cuda.synchronize()
 
-    # timed region: K steps, device-timed, clocks sampled
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.4)
+    sampler = None
+    if clocks:
+        # the steps back to back for about a second while nvidia-smi samples,
+        # then the timed region (a timed region of a few ms sees no sample)
+        sampler = ClockSampler(device.index or 0)
+        sampler.start()
+        t_load = time.time()
+        ms_one = max(timed(headline, 1, stream), 1e-3)
+        reps = max(1, int(1000.0 / ms_one))
+        while time.time() - t_load < 1.0:
+            for _ in range(reps):
+                headline()
+            torch.cuda.synchronize()
     barrier(pg)
     t_wall0 = time.time()
     torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler select the timed launches
-    ms_total = timed(headline, args.steps, stream)
+    ms_total = timed(headline, steps, stream, flush)
     torch.cuda.nvtx.range_pop()
     t_wall1 = time.time()
     barrier(pg)
-    sampler.mark(t_wall0, t_wall1)
-    clocks = sampler.stop()
+    clk = None
+    if sampler is not None:
+        sampler.mark(t_load, t_wall1)
+        clk = sampler.stop()
+    res_host = wl.res.cpu().tolist()
     ms_total = max_over_ranks(pg, ms_total, device)
-    ms_step = ms_total / args.steps
-    value = world * wl.cells * args.steps / (ms_total * 1e-3) / 1e9
+    ms_step = ms_total / steps
 
     # dominant kernel: the same K steps again with a CUDA event pair recorded
-    # by the library around every launch on this stream
+    # by the library around every launch on this stream (steps of one tile
+    # launch each time exactly that launch)
     ctx.profile_start()
-    for _ in range(args.steps):
+    for _ in range(steps):
         if batch_headline:
             wl.batch_step(ms, ctx, prep, sp)
         else:
@@ -551,45 +615,43 @@ def run_ours(args, world, rank, local, pg):
     prof = ctx.profile_stop()
     peak, peak_kind = measured_peaks()
     roof = None
-    if prof.other_ms > prof.tile_ms:
-        kern_ms, kern_launches, kern_name = prof.other_ms, prof.other_launches, \
-            "k_bits_search (bitplane doubling + binary search)"
-    else:
-        kern_ms, kern_launches, kern_name = prof.tile_ms, prof.tile_launches, \
-            ("k_batch_tiles (persistent tile queue)" if batch_headline
-             else "k_bitiles_one (bitplane tile pass)"
-             if prof.bit_tile_launches == prof.tile_launches
-             else "k_tiles_one (dp-recurrence tile pass)"
-             if prof.bit_tile_launches == 0 else "k_tiles_one + k_bitiles_one (tile passes)")
+    batch_label = batch_headline
+    kern_ms, kern_launches = ((prof.other_ms, prof.other_launches)
+                              if prof.other_ms > prof.tile_ms
+                              else (prof.tile_ms, prof.tile_launches))
+    alg_step = wl.cells * wl.bytes_per_cell
     if kern_launches and kern_ms > 0:
-        alg_bytes = wl.cells * wl.bytes_per_cell * args.steps
-        achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
-        traffic = profile_traffic(args.workload)
+        achieved = alg_step * steps / (kern_ms * 1e-3) / 1e9
+        traffic = profile_traffic(name)
+        per_launch_cells = wl.cells * steps / kern_launches
+        step_achieved = alg_step / (ms_step * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak,
                 "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs)"
                                 if peak_kind == "measured" else "of fallback 6800 GB/s"),
-                "traffic": (traffic * wl.cells if traffic is not None else None),
-                "kernel": kern_name, "bytes_per_cell": wl.bytes_per_cell,
-                "launches_per_step": kern_launches / args.steps,
-                "kernel_ms_per_step": kern_ms / args.steps,
-                "tile_ms_per_step": prof.tile_ms / args.steps,
-                "fixup_ms_per_step": prof.fixup_ms / args.steps,
-                "search_ms_per_step": prof.other_ms / args.steps,
-                "how": "per-launch CUDA events on the launching stream, same K steps re-run"}
-    launches_per_step = (prof.tile_launches + prof.fixup_launches + prof.other_launches) \
-        / args.steps
-    if batch_headline:
-        launches_per_step += 0  # the graph replays the same launches (queue reset is a memset)
-    launches = int(round(launches_per_step * args.steps))
+                "traffic": (traffic * per_launch_cells if traffic is not None else None),
+                "kernel": kernel_label(prof, batch_label), "bytes_per_cell": wl.bytes_per_cell,
+                "launches_per_step": kern_launches / steps,
+                "kernel_ms_per_step": kern_ms / steps,
+                "step_achieved": step_achieved, "step_frac": step_achieved / peak,
+                "tile_ms_per_step": prof.tile_ms / steps,
+                "fixup_ms_per_step": prof.fixup_ms / steps,
+                "search_ms_per_step": prof.other_ms / steps,
+                "how": "frac: algorithmic bytes / the dominant kernel's CUDA-event time "
+                       "(event pair around each of its launches on the launching stream, "
+                       "same K steps re-run); step_frac: algorithmic bytes / ms_per_step "
+                       "(the whole call)"}
+        if kern_ms / steps > ms_step * 1.02:
+            roof["note"] = ("per-launch event pairs between many short launches add gaps; "
+                            "the kernel time here is an upper bound")
+    launches = int(prof.tile_launches + prof.fixup_launches + prof.other_launches)
 
-    # batched vs plain, same matrices
     compare = None
     if multi:
         other = plain if batch_headline else batched
         for _ in range(2):
             other()
-        oms = timed(other, args.steps, stream) / args.steps
+        oms = timed(other, steps, stream, flush) / steps
         compare = {"plain" if batch_headline else "batched_graph": {
             "value": wl.cells / (oms * 1e-3) / 1e9, "unit": "Gcells/s", "ms_per_step": oms,
             "how": ("one ms_max_square call per matrix, eager launches" if batch_headline else
@@ -598,13 +660,27 @@ def run_ours(args, world, rank, local, pg):
     if plain_tuned:
         compare = dict(compare or {}, plain_autotuned=plain_tuned)
 
-    # e2e: pinned host inputs copied to fixed device buffers, the public call
-    # (ms_max_square per matrix, or ms_batch), results read back, per step.
-    # Plain calls: the copies run on a copy stream and each matrix's call
-    # waits for its own copy only, so copies overlap earlier matrices' calls
-    # (a host link of about 210 GB/s makes the copies the longer part).
-    # (the batch's matrices live in one pinned host arena and one device arena,
-    # 256-byte aligned, so that a step's input is one copy, not 4096)
+    e2e_d = None
+    if e2e:
+        e2e_d = measure_e2e(args, ms, ctx, wl, device, stream, pg, steps)
+
+    out = {"wl": wl, "value": wl.cells * steps / (ms_total * 1e-3) / 1e9, "ms_step": ms_step,
+           "roofline": roof, "launches": launches, "compare": compare, "clocks": clk,
+           "e2e": e2e_d, "results": res_host,
+           "status_ok": all(r[3] == 0 for r in res_host)}
+    return out
+
+
+def measure_e2e(args, ms, ctx, wl, device, stream, pg, steps):
+    """e2e: pinned host inputs copied to fixed device buffers, the public call
+    (ms_max_square / ms_dp_map per matrix, or ms_batch), results read back,
+    per step.  Plain calls: the copies run on a copy stream and each matrix's
+    call waits for its own copy only, so copies overlap earlier matrices'
+    calls.  A batch's matrices live in one pinned host arena and one device
+    arena (256-byte aligned), so a step's input is one copy."""
+    import torch
+    sp = stream.cuda_stream or None
+    batch_headline = wl.batch_headline
     h2d_bytes = wl.h2d_bytes()
     if batch_headline:
         offs, total = [], 0
@@ -621,7 +697,7 @@ def run_ours(args, world, rank, local, pg):
         h2d_bytes = total
     else:
         bufs = [torch.empty_like(mt.dev) for mt in wl.mats]
-    eprep = wl.prepare(ms, ctx, tensors=bufs)
+    eprep = wl.prepare(ms, tensors=bufs)
     res_host = torch.empty(wl.res.shape, dtype=torch.int32, pin_memory=True)
     copy_stream = torch.cuda.Stream(device)
     copied = [torch.cuda.Event() for _ in wl.mats]
@@ -644,91 +720,163 @@ def run_ours(args, world, rank, local, pg):
     for _ in range(max(1, args.warmup)):
         e2e_step()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         e2e_step()
     e2e_ms = max_over_ranks(pg, (time.perf_counter() - t0) * 1e3, device)
-    e2e = {"value": world * wl.cells * args.steps / (e2e_ms * 1e-3) / 1e9, "unit": "Gcells/s",
-           "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": res_host.numel() * 4,
-           "how": ("the batch's pinned host arena copied H2D in one copy, the public ms_batch "
-                   "call, results read back"
-                   if batch_headline else
-                   "pinned host inputs copied H2D on a copy stream (matrix i's call waits for "
-                   "its own copy), one public ms_* call per matrix, results read back")}
-
-    ok = bool((wl.res[:, 3] == 0).all().item())
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(wl.specs)
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "Gcells/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": wl.dtype, "data": "synthetic (seeded SplitMix64 Bernoulli matrices)",
-                "config": {**wl.config(), "parallelism": f"replicas x{world}",
-                           "packed_path": packed_path,
-                           **({"band_rows": args.band_rows} if args.band_rows else {}),
-                           **({"lane_cols": args.lane_cols} if args.lane_cols else {}),
-                           **({"tile_kind": args.tile_kind} if args.tile_kind else {}),
-                           "timed_path": ("ms_batch, CUDA graph replay" if batch_headline
-                                          else "one ms_* call per matrix (plain)")},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks, "compare": compare,
-                "status_ok": ok}
-        print(json.dumps(line), flush=True)
-    ctx.close()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    return {"value": world * wl.cells * steps / (e2e_ms * 1e-3) / 1e9, "unit": "Gcells/s",
+            "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": res_host.numel() * 4,
+            "how": ("the batch's pinned host arena copied H2D in one copy, the public ms_batch "
+                    "call, results read back"
+                    if batch_headline else
+                    "pinned host inputs copied H2D on a copy stream (matrix i's call waits for "
+                    "its own copy), one public ms_* call per matrix, results read back")}
 
 
-def run_serve(args, world, rank, local, pg):
-    """Serving stream: Poisson arrivals of `--requests` requests, square sides
-    log-uniform in [64, 8192], density uniform in [0.1, 0.9], bit-packed input
-    from pinned host memory, 16 GB device admission budget.  Payloads are
-    quantised to 24 side classes x 9 densities (kept pinned in host memory)."""
-    import numpy as np
+def leg_summary(r):
+    roof = r["roofline"] or {}
+    d = {"value": r["value"], "unit": "Gcells/s", "ms_per_step": r["ms_step"],
+         "kernel": roof.get("kernel"), "kernel_ms_per_step": roof.get("kernel_ms_per_step"),
+         "kernel_frac": roof.get("frac"), "step_frac": roof.get("step_frac"),
+         "bytes_per_cell": roof.get("bytes_per_cell"),
+         "fixup_ms_per_step": roof.get("fixup_ms_per_step"),
+         "launches_per_step": r["launches"] / max(1, r.get("steps", 1)),
+         "status_ok": r["status_ok"]}
+    if r["compare"]:
+        d["compare"] = r["compare"]
+    return d
+
+
+def run_ours(args, world, rank, local, pg):
     import torch
 
-    import gen
     import paper_2503_18974_gb300 as ms
     device = torch.device(f"cuda:{local}")
     torch.cuda.set_device(device)
     ms.build()
-    rng = np.random.default_rng(5)
-    sides = np.unique(np.round(np.exp(np.linspace(np.log(64), np.log(8192), 24))).astype(int))
-    dens = np.arange(1, 10) / 10
-    nreq = args.requests
-    req_side = np.exp(rng.uniform(np.log(64), np.log(8192), nreq))
-    req_cls = np.abs(np.log(sides)[None, :] - np.log(req_side)[:, None]).argmin(1)
-    req_den = np.abs(dens[None, :] - rng.uniform(0.1, 0.9, nreq)[:, None]).argmin(1)
-    payload = {}
-    for c, d in set(zip(req_cls.tolist(), req_den.tolist())):
-        side = int(sides[c])
-        ldw = ((side + 31) // 32 + 3) // 4 * 4
-        dev = torch.empty((side, ldw), dtype=torch.int32, device=device)
-        gen.fill_bits_dev(dev.data_ptr(), side, side, ldw, float(dens[d]), 5000 + 16 * c + d)
-        host = torch.empty((side, ldw), dtype=torch.int32, pin_memory=True)
-        host.copy_(dev)
-        payload[(c, d)] = (host, dev, side)
+    stream = torch.cuda.current_stream()
+    name = args.workload
+    verify = rank == 0 and not args.no_verify
+
+    head = measure(args, ms, name, device, stream, pg, clocks=True, e2e=True)
+    head["steps"] = args.steps
+    wl = head["wl"]
+
+    legs = {}
+    if name == "c3-u8" and not args.no_compare:
+        del wl.mats
+        head["wl"] = None
+        torch.cuda.empty_cache()
+        for leg in ("c3-u8-dp", "c3-bits", "c3-bits-dp", "c4"):
+            r = measure(args, ms, leg, device, stream, pg)
+            r["steps"] = args.steps
+            legs[leg] = r
+            r["wl"] = None
+            torch.cuda.empty_cache()
+
+    # the oracle side, after every timed region (its host threads would
+    # compete with the launching thread): the same matrices drawn on the host
+    verified = None
+    cpu = None
+    if verify or (rank == 0 and world == 1 and not args.no_cpu):
+        mats = host_matrices(workload_specs(name))
+        if verify:
+            exp = oracle_results(mats)
+            verified = {name: {"checked": len(exp),
+                               "wrong": sum(1 for g, e in zip(head["results"], exp)
+                                            if g != e + [0])}}
+            for leg, r in legs.items():
+                if leg.startswith("c3"):
+                    verified[leg] = {"checked": 1, "wrong": int(r["results"][0] != exp[0] + [0])}
+            if "c4" in legs:
+                c4m = host_matrices(workload_specs("c4"))
+                e4 = oracle_results(c4m)
+                del c4m
+                verified["c4"] = {"checked": len(e4),
+                                  "wrong": sum(1 for g, e in zip(legs["c4"]["results"], e4)
+                                               if g != e + [0])}
+            verified["how"] = ("every result of the last timed step against Algorithm 1 "
+                               "(oracle_freq) on the same matrices drawn on the host")
+        if rank == 0 and world == 1 and not args.no_cpu:
+            cpu = cpu_baseline(workload_specs(name), name, full=mats)
+        del mats
+
+    if rank == 0:
+        roof = head["roofline"]
+        compare = head["compare"] or {}
+        for leg, r in legs.items():
+            compare[leg] = leg_summary(r)
+        if "c4" in legs and legs["c4"]["compare"]:
+            c4 = legs["c4"]
+            plain = c4["compare"].get("plain", {}).get("value")
+            if plain:
+                compare["c4"]["batched_vs_plain"] = c4["value"] / plain
+        line = {"metric": METRIC, "value": head["value"], "unit": "Gcells/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": wl.dtype, "data": "synthetic (seeded SplitMix64 Bernoulli matrices)",
+                "config": {**wl.config(), "parallelism": f"replicas x{world}",
+                           **({"packed_path": args.packed_path}
+                              if args.packed_path is not None else {}),
+                           **({"band_rows": args.band_rows} if args.band_rows else {}),
+                           **({"lane_cols": args.lane_cols} if args.lane_cols else {}),
+                           **({"tile_kind": args.tile_kind} if args.tile_kind else {}),
+                           "timed_path": ("ms_batch, CUDA graph replay" if wl.batch_headline
+                                          else "one ms_* call per matrix (plain)")},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": head["e2e"],
+                "gpu_launches": head["launches"], "clocks": head["clocks"], "compare": compare,
+                "status_ok": head["status_ok"] and all(r["status_ok"] for r in legs.values()),
+                "verified_vs_oracle": verified}
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ serving ---
+
+def run_serve(args, world, rank, local, pg):
+    """Serving stream: Poisson arrivals of `--requests` requests, each its own
+    seeded square matrix (side log-uniform in [64, 8192], density uniform in
+    [0.1, 0.9]), bit-packed, from pinned host memory, 16 GB device admission
+    budget.  The saturated rate is measured first, then --serve-runs runs at
+    each of 0.5, 0.7 and 0.9 of it; every result is checked against the
+    oracle; the per-request plain baseline serves the same stream FIFO."""
+    import numpy as np
+    import torch
+
+    import paper_2503_18974_gb300 as ms
+    from gen import configs
+    device = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(device)
+    ms.build()
+    specs = configs.c5_specs(args.requests)
+    nreq = len(specs)
+    cells = sum(s["m"] * s["n"] for s in specs)
+
+    # every request's packed payload, drawn on the device, in one pinned arena
+    ldws = [round_up((s["n"] + 31) // 32, 4) for s in specs]
+    offs = np.cumsum([0] + [s["m"] * w for s, w in zip(specs, ldws)])
+    arena = torch.empty(int(offs[-1]), dtype=torch.int32, pin_memory=True)
+    stage = torch.empty(max(s["m"] * w for s, w in zip(specs, ldws)), dtype=torch.int32,
+                        device=device)
+    import gen
+    hosts = []
+    for k, (s, w) in enumerate(zip(specs, ldws)):
+        d = stage[:s["m"] * w].view(s["m"], w)
+        gen.fill_bits_dev(d.data_ptr(), s["m"], s["n"], w, s["p"], s["seed"])
+        h = arena[int(offs[k]):int(offs[k + 1])].view(s["m"], w)
+        h.copy_(d)
+        hosts.append(h)
     torch.cuda.synchronize()
-    cells = sum(int(sides[c]) ** 2 for c in req_cls)
+    descs = [ms.host_describe(h, n=s["n"]) for h, s in zip(hosts, specs)]
 
-    # prebuilt host descriptors (the payload tensors stay alive throughout)
-    descs = {key: ms.host_describe(host, n=side) for key, (host, _, side) in payload.items()}
-
-    # results alone (the reference for "same alone and in the mix")
-    ctx = ms.MaxSquare(local)
-    alone = {}
-    for key, (host, dev, side) in payload.items():
-        alone[key] = ctx.max_square(dev, n=side).cpu().tolist()
+    rng = np.random.default_rng(5)
 
     def serve(rate):
         srv = ms.Server(local, memory_budget=16 << 30, streams=3, max_batch=512)
-        srv.submit(payload[(req_cls[0], req_den[0])][0].numpy()[:1], n=64)  # warm
+        srv.submit(hosts[0].numpy()[:1], n=64)  # warm
         srv.wait_all()
         srv.poll()
         t0 = ms.now() + 0.01
         arrivals = t0 + (np.cumsum(rng.exponential(1.0 / rate, nreq)) if rate else np.zeros(nreq))
-        keys = [(int(req_cls[k]), int(req_den[k])) for k in range(nreq)]
         arr_list = [float(x) for x in arrivals]
         ids = {}
         now = ms.now
@@ -740,7 +888,7 @@ def run_serve(args, world, rank, local, pg):
             if rate:
                 while now() < arr_list[k]:
                     pass
-            ids[sub(descs[keys[k]], arr_list[k])] = keys[k]
+            ids[sub(descs[k], arr_list[k])] = k
         submit_s = now() - ts0
         srv.wait_all()
         done = srv.poll(nreq + 10)
@@ -748,67 +896,92 @@ def run_serve(args, world, rank, local, pg):
         srv.close()
         lat = np.array([c["t_done"] - c["t_submit"] for c in done])
         span = max(c["t_done"] for c in done) - float(arrivals[0])
-        wrong = sum(1 for c in done if c["result"] != alone[ids[c["id"]]])
+        results = {ids[c["id"]]: c["result"] for c in done}
         return {"cells_per_s": cells / span, "req_per_s": nreq / span, "span_s": span,
                 "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat, 99) * 1e3), "wrong": wrong,
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "batches": st["batches"], "peak_bytes": st["peak_bytes"],
                 "peak_inflight": st["peak_inflight"], "completed": len(done),
                 "client_submit_s": submit_s, "server_host_batch_s": st["host_batch_s"],
-                "server_host_copy_s": st["host_copy_s"]}
+                "server_host_copy_s": st["host_copy_s"], "_results": results}
 
     sat = serve(0)
-    runs = {}
-    clocks = None
+    runs, clocks = {}, None
+    all_results = [sat.pop("_results")]
     for f in (0.5, 0.7, 0.9):
-        if f == 0.7:  # the headline run: clocks sampled while it serves
-            sampler = ClockSampler(local)
-            sampler.start()
-            time.sleep(0.4)
-            tw0 = time.time()
-            runs["0.7x"] = serve(f * sat["req_per_s"])
-            sampler.mark(tw0, time.time())
-            clocks = sampler.stop()
-        else:
-            runs[f"{f}x"] = serve(f * sat["req_per_s"])
+        reps = []
+        for rep in range(args.serve_runs):
+            headline = f == 0.7 and rep == 0
+            if headline:  # clocks sampled while the headline run serves
+                sampler = ClockSampler(local)
+                sampler.start()
+                time.sleep(0.4)
+                tw0 = time.time()
+            r = serve(f * sat["req_per_s"])
+            if headline:
+                sampler.mark(tw0, time.time())
+                clocks = sampler.stop()
+            all_results.append(r.pop("_results"))
+            reps.append(r)
+        runs[f"{f}x"] = {"runs": reps,
+                         "p50_ms_median": float(np.median([r["p50_ms"] for r in reps])),
+                         "p99_ms_median": float(np.median([r["p99_ms"] for r in reps])),
+                         "cells_per_s_median": float(np.median([r["cells_per_s"]
+                                                               for r in reps]))}
 
-    # per-request plain launches, FIFO: copy in, ms_max_square, read back
-    buf = torch.empty(max(h.numel() for h, _, _ in payload.values()), dtype=torch.int32,
-                      device=device)
+    # per-request plain launches over the same stream, FIFO: copy in,
+    # ms_max_square, read back, one request at a time
+    ctx = ms.MaxSquare(local)
+    buf = torch.empty(stage.numel(), dtype=torch.int32, device=device)
     res = torch.empty(4, dtype=torch.int32, device=device)
     res_h = torch.empty(4, dtype=torch.int32, pin_memory=True)
-    sub = min(nreq, 4000)
+    plain_results = {}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plain_cells = 0
-    for k in range(sub):
-        host, _, side = payload[(int(req_cls[k]), int(req_den[k]))]
-        d = buf[:host.numel()].view(host.shape)
-        d.copy_(host, non_blocking=True)
-        ctx.max_square(d, n=side, out=res)
+    for k, (h, s) in enumerate(zip(hosts, specs)):
+        d = buf[:h.numel()].view(h.shape)
+        d.copy_(h, non_blocking=True)
+        ctx.max_square(d, n=s["n"], out=res)
         res_h.copy_(res, non_blocking=True)
         torch.cuda.synchronize()
-        plain_cells += side * side
-    plain = plain_cells / (time.perf_counter() - t0)
+        plain_results[k] = res_h.tolist()
+    plain_s = time.perf_counter() - t0
     ctx.close()
-    r7 = runs["0.7x"]
+
+    # the oracle on every request (host-drawn matrices), in host threads,
+    # after the timed runs
+    import oracle
+    oracle.build()
+    with cf.ThreadPoolExecutor(HOST_THREADS) as pool:
+        exp = list(pool.map(lambda s: [*oracle.freq(gen.config_u8(s)), 0], specs))
+    wrong = sum(1 for rr in all_results for k, v in rr.items() if v != exp[k])
+    missing = sum(1 for rr in all_results if len(rr) != nreq)
+    wrong_plain = sum(1 for k, v in plain_results.items() if v != exp[k])
+    r7 = runs["0.7x"]["runs"][0]
     if rank == 0:
         line = {"metric": METRIC, "value": r7["cells_per_s"] / 1e9, "unit": "Gcells/s",
                 "n_gpus": world, "steps": 1, "warmup": 1,
                 "ms_per_step": r7["span_s"] * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "bits32",
-                "data": "synthetic (seeded SplitMix64 Bernoulli matrices)",
+                "data": "synthetic (seeded SplitMix64 Bernoulli matrices, one per request)",
                 "config": {"workload": f"serving stream: {nreq} Poisson requests at 0.7x the "
-                                       "saturated rate, sides log-uniform 64..8192, p in "
-                                       "0.1..0.9, bit-packed, 16 GB admission budget",
-                           "payload_classes": len(payload), "cells": cells},
+                                       "saturated rate, sides log-uniform 64..8192, p uniform "
+                                       "in [0.1, 0.9], each request its own matrix, "
+                                       "bit-packed, 16 GB admission budget",
+                           "cells": cells, "payload_bytes": int(offs[-1]) * 4},
                 "serve": {"saturated": sat, **runs},
-                "p50_ms": r7["p50_ms"], "p99_ms": r7["p99_ms"],
-                "plain_per_request": {"value": plain / 1e9, "unit": "Gcells/s",
-                                      "requests": sub,
-                                      "how": "FIFO, one H2D + ms_max_square + D2H per request"},
+                "p50_ms": runs["0.7x"]["p50_ms_median"], "p99_ms": runs["0.7x"]["p99_ms_median"],
+                "plain_per_request": {"value": cells / plain_s / 1e9, "unit": "Gcells/s",
+                                      "requests": nreq, "wrong_vs_oracle": wrong_plain,
+                                      "how": "the same stream FIFO, one H2D + ms_max_square + "
+                                             "D2H per request"},
+                "verified_vs_oracle": {"checked": sum(len(rr) for rr in all_results),
+                                       "wrong": wrong, "runs_missing_results": missing,
+                                       "how": "every completed request of every run against "
+                                              "Algorithm 1 (oracle_freq) on the host-drawn "
+                                              "matrix"},
                 "e2e": {"value": r7["cells_per_s"] / 1e9, "unit": "Gcells/s",
-                        "h2d_bytes_per_step": int(cells // 8),
+                        "h2d_bytes_per_step": int(offs[-1]) * 4,
                         "d2h_bytes_per_step": 16 * nreq,
                         "how": "requests submitted from pinned host memory; latency includes "
                                "queueing, copies and read-back"},
@@ -824,9 +997,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep")
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="c3-u8")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-verify", action="store_true", help="skip the oracle check")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="c3-u8: skip the dp-map, packed and batch legs")
     ap.add_argument("--requests", type=int, default=20000)
+    ap.add_argument("--serve-runs", type=int, default=3)
     ap.add_argument("--packed-path", type=int, default=None,
                     help="packed size-only work: 0 tile kernel, 1 bitplane search "
                          "(default: the autotuner's choice)")

@@ -62,6 +62,7 @@ def _lib():
         lib.msgen_thr24.restype = _u32
         lib.msgen_thr24.argtypes = [ctypes.c_double]
         lib.msgen_fill_u8.argtypes = [_vp, _i64, _i64, _i64, _u64, _u32]
+        lib.msgen_fill_u8_rows.argtypes = [_vp, _i64, _i64, _i64, _i64, _u64, _u32]
         lib.msgen_plant_pos.argtypes = [_u64, _i64, _i64, _i64, ctypes.POINTER(_i64),
                                         ctypes.POINTER(_i64)]
         lib.msgen_plant_u8.argtypes = [_vp, _i64, _i64, _i64, _i64]
@@ -95,13 +96,36 @@ def thr24(p: float) -> int:
     return int(_lib().msgen_thr24(p))
 
 
-def bernoulli_u8(m: int, n: int, p: float, seed: int, ld: int | None = None) -> np.ndarray:
-    """m x n uint8 0/1 matrix (as an m x ld array whose first n columns are the cells)."""
+def bernoulli_u8(m: int, n: int, p: float, seed: int, ld: int | None = None,
+                 threads: int = 1) -> np.ndarray:
+    """m x n uint8 0/1 matrix (as an m x ld array whose first n columns are the cells).
+    threads > 1 fills disjoint row ranges concurrently (same cells)."""
     ld = n if ld is None else ld
     out = np.zeros((m, max(ld, 1)), dtype=np.uint8)
-    if m > 0 and n > 0:
-        _lib().msgen_fill_u8(out.ctypes.data, m, n, ld, seed, thr24(p))
+    if m <= 0 or n <= 0:
+        return out
+    t = thr24(p)
+    if threads <= 1 or m < 2 * threads:
+        _lib().msgen_fill_u8(out.ctypes.data, m, n, ld, seed, t)
+        return out
+    import concurrent.futures as cf
+    lib, base = _lib(), out.ctypes.data
+    step = (m + threads - 1) // threads
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:  # ctypes drops the GIL
+        list(ex.map(lambda r0: lib.msgen_fill_u8_rows(base + r0 * ld, r0, min(m, r0 + step),
+                                                      n, ld, seed, t),
+                    range(0, m, step)))
     return out
+
+
+def config_u8(spec: dict, threads: int = 1) -> np.ndarray:
+    """The uint8 matrix of a workload recipe (see ``gen.configs``): Bernoulli
+    cells plus the planted square, if any."""
+    a = bernoulli_u8(spec["m"], spec["n"], spec["p"], spec["seed"], threads=threads)
+    if spec.get("plant"):
+        r, c = plant_pos(spec["seed"], spec["m"], spec["n"], spec["plant"])
+        a[r:r + spec["plant"], c:c + spec["plant"]] = 1
+    return a
 
 
 def plant_pos(seed: int, m: int, n: int, s: int) -> tuple[int, int]:

@@ -24,9 +24,14 @@ uint32_t msgen_thr24(double p) {
 }
 
 void msgen_fill_u8(uint8_t* out, int64_t m, int64_t n, int64_t ld, uint64_t seed, uint32_t thr24) {
+  msgen_fill_u8_rows(out, 0, m, n, ld, seed, thr24);
+}
+
+void msgen_fill_u8_rows(uint8_t* out, int64_t r0, int64_t r1, int64_t n, int64_t ld,
+                        uint64_t seed, uint32_t thr24) {
   const uint64_t key = msgen_mix64(seed);
-  for (int64_t i = 0; i < m; ++i) {
-    uint8_t* row = out + i * ld;
+  for (int64_t i = r0; i < r1; ++i) {
+    uint8_t* row = out + (i - r0) * ld;
     uint64_t k = (uint64_t)(i * n);
     for (int64_t j = 0; j < n; ++j, ++k) {
       uint64_t z = msgen_mix64(key + (k + 1) * MSGEN_GAMMA);

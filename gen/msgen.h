@@ -35,6 +35,10 @@ uint32_t msgen_thr24(double p);
 
 /* Bernoulli(thr24 / 2^24) cells into a row-major uint8 matrix (values 0/1). */
 void msgen_fill_u8(uint8_t* out, int64_t m, int64_t n, int64_t ld, uint64_t seed, uint32_t thr24);
+/* Rows r0 <= i < r1 of the same matrix (any m > i), row i written at
+ * out + (i - r0) * ld: disjoint row ranges can be filled concurrently. */
+void msgen_fill_u8_rows(uint8_t* out, int64_t r0, int64_t r1, int64_t n, int64_t ld,
+                        uint64_t seed, uint32_t thr24);
 /* Top-left corner of a planted s x s square, uniform over [0,m-s] x [0,n-s],
  * from draws m*n (row) and m*n+1 (column): r = ((draw>>32) * (m-s+1)) >> 32. */
 void msgen_plant_pos(uint64_t seed, int64_t m, int64_t n, int64_t s, int64_t* r, int64_t* c);

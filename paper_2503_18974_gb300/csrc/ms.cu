@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "ms_bitile.cuh"
@@ -127,16 +128,20 @@ struct DeviceGuard {
 // Dynamic shared memory of a tile kernel launch: one input ring per warp.
 size_t ring_bytes(int threads) { return (size_t)(threads / 32) * ms::kRingWarpBytes; }
 
-// Raise a kernel's dynamic shared memory limit once (the rings exceed 48 KB).
+// Raise a kernel's dynamic shared memory limit once per device (the rings
+// exceed 48 KB; the attribute belongs to the current device's context).
 cudaError_t allow_smem(const void* fn, size_t bytes) {
   static std::mutex mu;
-  static std::map<const void*, size_t> done;
+  static std::map<std::pair<const void*, int>, size_t> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaGetLastError();
   std::lock_guard<std::mutex> lk(mu);
-  auto it = done.find(fn);
+  const auto key = std::make_pair(fn, dev);
+  auto it = done.find(key);
   if (it != done.end() && it->second >= bytes) return cudaSuccess;
   const cudaError_t e =
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess) done[fn] = bytes;
+  if (e == cudaSuccess) done[key] = bytes;
   return e;
 }
 

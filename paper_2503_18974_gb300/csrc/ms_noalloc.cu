@@ -18,8 +18,11 @@
 //
 // In host code the array's name is only a host-side stand-in, not a device
 // address, so the first call on each device looks up the array's real
-// address with cudaGetSymbolAddress (with that device current) and keeps it;
-// later calls on that device reuse it.
+// address with cudaGetSymbolAddress (with that device current) and keeps it,
+// with the device's context; later calls in that context reuse it, and a
+// call in a new context of the device (after cudaDeviceReset) looks it up
+// again.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -78,10 +81,43 @@ __global__ void __launch_bounds__(ms::kFixWarps * 32, 1) k_noalloc_fixup(const m
   ms::fixup_job<FMT, false>(job);
 }
 
-std::mutex g_mu;
-unsigned char* g_addr[kMaxDevices] = {};
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
+// The driver's cuCtxGetCurrent, through the runtime's entry-point query (no
+// link-time dependency on the driver library).
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+template <int FMT>
+cudaError_t allow_smem_all();
+
+// Per device: the context the set-up was made in, the scratch array's device
+// address in it, and whether the kernels' shared-memory limits are raised.
+struct DeviceSetup {
+  CUcontext ctx = nullptr;
+  unsigned char* addr = nullptr;
+};
+std::mutex g_mu;
+DeviceSetup g_setup[kMaxDevices];
+
+// Device address of g_noalloc_scratch on the current device.  The set-up
+// (cudaGetSymbolAddress with the device current, and the kernels'
+// shared-memory limits) runs on the first call on a device, and again when
+// the device's context has changed since (after cudaDeviceReset the module is
+// loaded anew and the array may sit at another address).
 ms_status scratch_address(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -89,17 +125,35 @@ ms_status scratch_address(unsigned char** out) {
     return MS_ERR_CUDA;
   }
   if (dev < 0 || dev >= kMaxDevices) return MS_ERR_UNSUPPORTED;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return MS_ERR_CUDA;
+  // (null before the runtime has made the device's context current in this
+  // thread: the set-up below does that)
+  CUcontext cur = nullptr;
+  if (get(&cur) != CUDA_SUCCESS) cur = nullptr;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  DeviceSetup& d = g_setup[dev];
+  if (!d.addr || !cur || d.ctx != cur) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
+      d.addr = nullptr;
       return MS_ERR_CUDA;
     }
-    g_addr[dev] = static_cast<unsigned char*>(p);
+    if (allow_smem_all<MS_U8>() != cudaSuccess || allow_smem_all<MS_BITS32>() != cudaSuccess) {
+      cudaGetLastError();
+      d.addr = nullptr;
+      return MS_ERR_CUDA;
+    }
+    if (get(&cur) != CUDA_SUCCESS || !cur) {
+      d.addr = nullptr;
+      return MS_ERR_CUDA;
+    }
+    d.addr = static_cast<unsigned char*>(p);
+    d.ctx = cur;
   }
-  *out = g_addr[dev];
+  *out = d.addr;
   return MS_OK;
 }
 
@@ -116,17 +170,31 @@ cudaError_t allow_smem(const void* fn, int bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
+constexpr int kTileSmem = (kThreads / 32) * ms::kRingWarpBytes;
+constexpr int kFixSmem = ms::kFixWarps * ms::kRingWarpBytes;
+
+// Every kernel of one format, for the current device (part of the set-up).
+template <int FMT>
+cudaError_t allow_smem_all() {
+  cudaError_t e = allow_smem((const void*)k_noalloc_tiles<1, FMT>, kTileSmem);
+  if (e == cudaSuccess) e = allow_smem((const void*)k_noalloc_tiles<2, FMT>, kTileSmem);
+  if (e == cudaSuccess) e = allow_smem((const void*)k_noalloc_tiles<4, FMT>, kTileSmem);
+  if (e == cudaSuccess) e = allow_smem((const void*)k_noalloc_tiles<8, FMT>, kTileSmem);
+  if (e == cudaSuccess) e = allow_smem((const void*)k_noalloc_tiles<16, FMT>, kTileSmem);
+  if (e == cudaSuccess) e = allow_smem((const void*)k_noalloc_fixup<FMT>, kFixSmem);
+  return e;
+}
+
+// (the kernels' shared-memory limits were raised by the device's set-up)
 template <int FMT>
 cudaError_t launch(const ms::Job& j, int64_t ntiles, cudaStream_t s) {
   if (ntiles > 0) {
     const int64_t warps = (ntiles + 1) / 2;
     const unsigned grid = (unsigned)((warps + kThreads / 32 - 1) / (kThreads / 32));
-    const int sm = (kThreads / 32) * ms::kRingWarpBytes;
+    const int sm = kTileSmem;
     switch (j.P) {
 #define MS_NOALLOC_TILES(PP)                                                      \
   case PP:                                                                        \
-    if (allow_smem((const void*)k_noalloc_tiles<PP, FMT>, sm) != cudaSuccess)     \
-      return cudaGetLastError();                                                  \
     k_noalloc_tiles<PP, FMT><<<grid, kThreads, sm, s>>>(j, ntiles);               \
     break;
       MS_NOALLOC_TILES(1)
@@ -138,9 +206,7 @@ cudaError_t launch(const ms::Job& j, int64_t ntiles, cudaStream_t s) {
 #undef MS_NOALLOC_TILES
     }
   }
-  const int smf = ms::kFixWarps * ms::kRingWarpBytes;
-  if (allow_smem((const void*)k_noalloc_fixup<FMT>, smf) != cudaSuccess) return cudaGetLastError();
-  k_noalloc_fixup<FMT><<<1, ms::kFixWarps * 32, smf, s>>>(j);
+  k_noalloc_fixup<FMT><<<1, ms::kFixWarps * 32, kFixSmem, s>>>(j);
   return cudaGetLastError();
 }
 

@@ -372,15 +372,18 @@ ms_status ms_server_submit(ms_server* s, const ms_matrix* host, double t_arrival
     return MS_ERR_BUDGET;
   }
   r->t_submit = t_arrival >= 0 ? t_arrival : now_s();
+  uint64_t rid;
   {
     std::lock_guard<std::mutex> lk(s->mu);
-    r->id = s->next_id++;
+    rid = r->id = s->next_id++;
     s->pending.push_back(r);
     s->outstanding++;
     s->stats.submitted++;
   }
+  // (r belongs to the scheduler from here on: it may already be finished
+  // and freed, so only the local copy of its id is read)
   s->cv.notify_one();
-  *id = r->id;
+  *id = rid;
   return MS_OK;
 }
 

@@ -2,14 +2,17 @@
 device memory (for example plug-ins whose host application owns all device
 memory through its own pool, or services that must not allocate after
 start-up): called through the C ABI, it must give exactly the result of
-ms_max_square on the same inputs, on consecutive calls that reuse its fixed
-scratch array.  This file is named to be collected last."""
+ms_max_square on the same inputs, and the oracle's (the textbook DP of Eq. 1:
+side and first row-major corner), on consecutive calls that reuse its fixed
+scratch array, up to its largest accepted size (8192 x 8192).  This file is
+named to be collected last."""
 import ctypes
 
 import numpy as np
 import pytest
 
 import gen
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -53,11 +56,12 @@ def cases():
 def test_noalloc_matches_ms_max_square_on_consecutive_calls(libs):
     ms, L, ctx = libs
     for a in cases():
+        exp = [*oracle.dp(a, want_map=False)[0], 0]
         x = torch.from_numpy(a).to("cuda:0")
         ref = ctx.max_square(x)
         rc, got = noalloc(ms, L, x)
         assert rc == 0
-        assert got.cpu().tolist() == ref.cpu().tolist()
+        assert got.cpu().tolist() == ref.cpu().tolist() == exp
         n = a.shape[1]
         w = torch.from_numpy(gen.pack_bits(a, n, pad_value=1).view(np.int32)).to("cuda:0")
         ref_b = ctx.max_square(w, n=n)
