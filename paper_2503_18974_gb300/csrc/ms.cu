@@ -461,9 +461,15 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
     const int wpb = (int)std::min<int64_t>(ms::bt::kWarps, (ntiles + ctx->sms - 1) / ctx->sms);
     const unsigned grid = (unsigned)((ntiles + wpb - 1) / wpb);
     const size_t sm = (size_t)wpb * ms::bt::kWarpBytes;
-    if (allow_smem((const void*)ms::k_bitiles_one<FMT>, sm) != cudaSuccess)
-      return cudaGetLastError();
-    ms::k_bitiles_one<FMT><<<grid, 32 * wpb, sm, s>>>(j, ntiles, fuse);
+    if (fuse) {
+      if (allow_smem((const void*)ms::k_bitiles_one<FMT, true>, sm) != cudaSuccess)
+        return cudaGetLastError();
+      ms::k_bitiles_one<FMT, true><<<grid, 32 * wpb, sm, s>>>(j, ntiles);
+    } else {
+      if (allow_smem((const void*)ms::k_bitiles_one<FMT, false>, sm) != cudaSuccess)
+        return cudaGetLastError();
+      ms::k_bitiles_one<FMT, false><<<grid, 32 * wpb, sm, s>>>(j, ntiles);
+    }
   } else if (ntiles > 0) {
     ProfScope ps(ctx, s, kProfTile);
     const int64_t warps = (ntiles + 1) / 2;
@@ -816,11 +822,12 @@ ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes) {
     // input formats; the smaller count)
     const size_t sm = (size_t)ms::bt::kWarps * ms::bt::kWarpBytes;
     int b0 = 0, b1 = 0;
-    if (allow_smem((const void*)ms::k_bitiles_one<MS_U8>, sm) != cudaSuccess ||
-        allow_smem((const void*)ms::k_bitiles_one<MS_BITS32>, sm) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, ms::k_bitiles_one<MS_U8>,
+    // (the variants without the fused fix-up: the launches that fill the GPU)
+    if (allow_smem((const void*)ms::k_bitiles_one<MS_U8, false>, sm) != cudaSuccess ||
+        allow_smem((const void*)ms::k_bitiles_one<MS_BITS32, false>, sm) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, ms::k_bitiles_one<MS_U8, false>,
                                                       32 * ms::bt::kWarps, sm) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, ms::k_bitiles_one<MS_BITS32>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, ms::k_bitiles_one<MS_BITS32, false>,
                                                       32 * ms::bt::kWarps, sm) != cudaSuccess) {
       cudaGetLastError();
       b0 = b1 = 1;

@@ -357,7 +357,7 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
         }
         if (K >= kTop) {
           const uint32_t w = level_word(ring, lane, ir, kTop, lv[0]) & cm;
-          if (plane33 && cm) plane33[(g.wr0 + ir) * pw + (g.wc0 >> 5) + lane] = w;
+          if (plane33 && cm) st_keep_l2(plane33 + (g.wr0 + ir) * pw + (g.wc0 >> 5) + lane, w);
           const unsigned b = __ballot_sync(kFull, w != 0u);
           if (b) {
             const int L0 = __ffs(b) - 1, L1 = 31 - __clz(b);
@@ -409,14 +409,16 @@ __device__ __forceinline__ void tile_one(const Job& j, int64_t t) {
 }  // namespace bt
 
 // Size-only tile pass of one matrix by bitplanes (tile geometry of lane width
-// 32); fuse != 0: the last block also runs the bitplane fix-up of the box and
-// writes the result, from its own shared memory when the box fits.
-template <int FMT>
-__global__ void __launch_bounds__(256, 3) k_bitiles_one(const Job job, int64_t ntiles, int fuse) {
+// 32); FUSE: the last block also runs the bitplane fix-up of the box and
+// writes the result, from its own shared memory when the box fits (small
+// matrices; the large ones take the variant without that code, whose tile
+// loop then keeps every register to itself).
+template <int FMT, bool FUSE>
+__global__ void __launch_bounds__(256, 3) k_bitiles_one(const Job job, int64_t ntiles) {
   grid_dependents_may_launch();
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w < ntiles) bt::tile_one<FMT>(job, w);
-  if (fuse) {
+  if constexpr (FUSE) {
     __shared__ int s_last;
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -117,6 +117,16 @@ __device__ __forceinline__ uint32_t nonzero_msb(uint32_t x) {
   return ((x & 0x7f7f7f7fu) + 0x7f7f7f7fu) | x;
 }
 
+// A store asking L2 to keep its line (evict-last policy): for the few words
+// a kernel hands to the next one, which the streamed input would otherwise
+// push out of L2 before they are read.
+__device__ __forceinline__ void st_keep_l2(uint32_t* p, uint32_t v) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -1087,6 +1087,328 @@ __device__ __forceinline__ Plane gather_s33(const Job& j, int rlo, int rhi, int 
   return s;
 }
 
+// ---- size-only fix-up by one block with its planes in shared memory -----
+//
+// The common case (a single call's box, or a batch matrix's, that fits one
+// block's shared memory): the growth, search and witness of fixup_bits
+// below, specialised for one block.  Passes walk the active box of their
+// source plane with per-cell predicates and end with one block barrier; the
+// search tests several sides per pass while the plane is small.  The result
+// is the same: K = the largest t with S_t non-empty, witness = the first set
+// bit of S_K in row-major order.
+namespace sbox {
+
+constexpr int kWays = 7;          // sides tested per search pass, at most
+constexpr int kProbeBudget = 16;  // word tests per thread a search pass may take
+
+// A plane stored over rows [r0, r0 + rows) x words [w0, w0 + cols) of the
+// matrix in shared memory (row pitch `pitch` >= cols, odd so that threads
+// walking different rows meet different banks), zero outside its active box
+// [ar0, ar1) x [aw0, aw1).
+struct SP {
+  uint32_t* p;
+  int r0, w0, pitch, cols, rows;
+  int ar0, ar1, aw0, aw1;
+  __device__ __forceinline__ int base(int i) const { return (i - r0) * pitch - w0; }
+  __device__ __forceinline__ bool empty() const { return ar1 <= ar0 || aw1 <= aw0; }
+};
+
+__host__ __device__ __forceinline__ int odd_pitch(int cols) { return cols | 1; }
+
+// A rows x cols region cut into rows * nseg runs of at most `len`
+// consecutive words of one row; the block's threads take the runs with
+// stride blockDim (about one each).
+struct Runs {
+  int rows, cols, nseg, len;
+  __device__ __forceinline__ Runs(int r, int c) : rows(r), cols(c), nseg(0), len(0) {
+    if (r <= 0 || c <= 0) return;
+    nseg = max(1, min(c, (int)blockDim.x / r));
+    len = (c + nseg - 1) / nseg;
+    nseg = (c + len - 1) / len;
+  }
+  template <class F>
+  __device__ __forceinline__ void each(F&& f) const {
+    const int units = rows * nseg;
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+      const int r = u / nseg, c0 = (u - r * nseg) * len;
+      f(r, c0, min(cols, c0 + len));
+    }
+  }
+};
+
+// Words [wb, we) (inside L's active box) of row i of S_{a+d} from L = S_a
+// (0 <= d <= a): the AND of L at (i, col), (i-d, col), (i, col-d),
+// (i-d, col-d) for the words' 32 columns, reads left of or above L's active
+// box being zeros.  g(w, v) receives each word in order; the shifted reads of
+// one word are reused by the next.
+template <class G>
+__device__ __forceinline__ void grow_run(const SP& L, int i, int wb, int we, int d, G&& g) {
+  if (i - d < L.ar0) {  // the square's top row lies above every set bit
+    for (int w = wb; w < we; ++w) g(w, 0u);
+    return;
+  }
+  const int q = d >> 5, r = d & 31;
+  const uint32_t* __restrict__ p = L.p;
+  const int bi = L.base(i), bu = L.base(i - d);
+  int wq = wb - q;
+  uint32_t pb = wq - 1 >= L.aw0 ? p[bi + wq - 1] : 0u;
+  uint32_t pc = wq - 1 >= L.aw0 ? p[bu + wq - 1] : 0u;
+  for (int w = wb; w < we; ++w, ++wq) {
+    const bool ok = wq >= L.aw0;
+    const uint32_t b = ok ? p[bi + wq] : 0u;
+    const uint32_t c = ok ? p[bu + wq] : 0u;
+    g(w, p[bi + w] & p[bu + w] & __funnelshift_l(pb, b, r) & __funnelshift_l(pc, c, r));
+    pb = b;
+    pc = c;
+  }
+}
+
+// Block-wide fold of per-thread boxes through `part` ([32][4] shared ints;
+// callers alternate two such buffers between consecutive folds); every
+// thread receives [r0, r1) x [w0, w1) (empty: r1 <= r0).
+__device__ __forceinline__ void fold_box(int rmin, int rmax, int wmin, int wmax, int (*part)[4],
+                                         int out[4]) {
+  rmin = __reduce_min_sync(kFull, rmin);
+  rmax = __reduce_max_sync(kFull, rmax);
+  wmin = __reduce_min_sync(kFull, wmin);
+  wmax = __reduce_max_sync(kFull, wmax);
+  const int lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+  if (lane == 0) {
+    int* q = part[threadIdx.x >> 5];
+    q[0] = rmin;
+    q[1] = rmax;
+    q[2] = wmin;
+    q[3] = wmax;
+  }
+  __syncthreads();
+  int b0 = 0x7fffffff, b1 = -1, b2 = 0x7fffffff, b3 = -1;
+  if (lane < nw) {
+    b0 = part[lane][0];
+    b1 = part[lane][1];
+    b2 = part[lane][2];
+    b3 = part[lane][3];
+  }
+  out[0] = __reduce_min_sync(kFull, b0);
+  out[1] = __reduce_max_sync(kFull, b1) + 1;
+  out[2] = __reduce_min_sync(kFull, b2);
+  out[3] = __reduce_max_sync(kFull, b3) + 1;
+}
+
+// O = S_{a+d} from L = S_a over L's active box clipped to O's storage; sets
+// O's active box.
+__device__ __forceinline__ void grow_write(const SP& L, SP& O, int d, int (*part)[4]) {
+  const int r0 = max(L.ar0, O.r0), r1 = min(L.ar1, O.r0 + O.rows);
+  const int w0 = max(L.aw0, O.w0), w1 = min(L.aw1, O.w0 + O.cols);
+  int rmin = 0x7fffffff, rmax = -1, wmin = 0x7fffffff, wmax = -1;
+  uint32_t* __restrict__ op = O.p;  // (never the plane read)
+  Runs(r1 - r0, w1 - w0).each([&](int rr, int cb, int ce) {
+    const int i = r0 + rr, ob = O.base(i);
+    bool any = false;
+    grow_run(L, i, w0 + cb, w0 + ce, d, [&](int w, uint32_t v) {
+      op[ob + w] = v;
+      if (v) {
+        wmin = min(wmin, w);
+        wmax = max(wmax, w);
+        any = true;
+      }
+    });
+    if (any) {
+      rmin = min(rmin, i);
+      rmax = max(rmax, i);
+    }
+  });
+  int box[4];
+  fold_box(rmin, rmax, wmin, wmax, part, box);
+  O.ar0 = box[0];
+  O.ar1 = box[1];
+  O.aw0 = box[2];
+  O.aw1 = box[3];
+}
+
+// Bit k of the result (k < T <= kWays): S_{t_k} has a set bit, for the T
+// sides t_k = lo + (k+1) * span / (T+1) tested from L = S_a (t_k - a <= a).
+// A corner of a t-square is a corner of every smaller square, so each run
+// tests the sides from the largest down and stops at its first hit.
+__device__ __forceinline__ unsigned probe(const SP& L, int a, int lo, int span, int T,
+                                          int (*part)[4]) {
+  // (32-bit: span * kWays < 2^31 for every supported side)
+  int d[kWays];
+  const unsigned q = (unsigned)span / (unsigned)(T + 1), rem = (unsigned)span % (unsigned)(T + 1);
+#pragma unroll
+  for (int k = 0; k < kWays; ++k)
+    d[k] = lo + (int)(q * (k + 1) + (rem * (k + 1)) / (unsigned)(T + 1)) - a;
+  unsigned mask = 0u;
+  Runs(L.ar1 - L.ar0, L.aw1 - L.aw0).each([&](int rr, int cb, int ce) {
+    const int i = L.ar0 + rr;
+#pragma unroll
+    for (int k = kWays - 1; k >= 0; --k) {
+      if (k >= T || (mask >> k & 1u)) continue;
+      uint32_t hit = 0u;
+      grow_run(L, i, L.aw0 + cb, L.aw0 + ce, d[k], [&](int, uint32_t v) { hit |= v; });
+      if (hit) {
+        mask |= (2u << k) - 1u;
+        break;
+      }
+    }
+  });
+  mask = __reduce_or_sync(kFull, mask);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5][0] = (int)mask;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  return __reduce_or_sync(kFull, lane < (int)(blockDim.x >> 5) ? (unsigned)part[lane][0] : 0u);
+}
+
+// The first set bit (row-major index i*n + col) of S_{a+d} from L = S_a, or
+// ~0; every set bit is appended to the corner list when `emit` is given.
+__device__ __forceinline__ unsigned long long first_bit(const SP& L, int d, int64_t n,
+                                                        unsigned long long* s_first,
+                                                        const Job* emit) {
+  unsigned long long f = ~0ull;
+  Runs(L.ar1 - L.ar0, L.aw1 - L.aw0).each([&](int rr, int cb, int ce) {
+    const int i = L.ar0 + rr;
+    grow_run(L, i, L.aw0 + cb, L.aw0 + ce, d, [&](int w, uint32_t v) {
+      if (!v) return;
+      const unsigned long long cand = (unsigned long long)i * (unsigned long long)n +
+                                      (unsigned long long)(32 * (int64_t)w) +
+                                      (unsigned long long)(__ffs(v) - 1);
+      f = cand < f ? cand : f;
+      if (emit)
+        for (uint32_t b = v; b; b &= b - 1)
+          emit_corner(*emit, i, 32 * (int64_t)w + (__ffs(b) - 1));
+    });
+  });
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(kFull, f, o);
+    f = v < f ? v : f;
+  }
+  if ((threadIdx.x & 31) == 0 && f != ~0ull) atomicMin(s_first, f);
+  __syncthreads();
+  return *reinterpret_cast<volatile unsigned long long*>(s_first);
+}
+
+// S_33 of rows [rlo, rhi) x words [wlo, whi) from the bitplane tiles' rows
+// (job.first33 set: a word counts where its tile had reached its first S_33
+// row, zero elsewhere) into `out` (shared, pitch odd_pitch(whi - wlo)).  The
+// threads take the cells in row-major order (coalesced reads) and each
+// issues the global reads of kBatch of its cells before using any of them.
+__device__ __forceinline__ SP gather33(const Job& j, int rlo, int rhi, int wlo, int whi,
+                                      uint32_t* out, int (*part)[4]) {
+  constexpr int kBatch = 8;
+  const int64_t pw = (j.n + 31) / 32;
+  const uint32_t* raw = j.bits_scratch + 2 * j.m * (pw + 2);
+  const int BW = whi - wlo, rows = rhi - rlo, P = odd_pitch(BW);
+  // tiles are 32 words wide; a later strip counts 31 (its first is halo)
+  const int br = j.band_rows;
+  const float inv_br = 1.0f / (float)br;
+  int rmin = 0x7fffffff, rmax = -1, wmin = 0x7fffffff, wmax = -1;
+  const int bd = (int)blockDim.x;
+  const int dr = bd / BW, dc = bd - dr * BW;
+  int r = (int)threadIdx.x / BW, c = (int)threadIdx.x - r * BW;
+  while (r < rows) {
+    int rk[kBatch], ck[kBatch], f[kBatch];
+    uint32_t rv[kBatch];
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k) {
+      rk[k] = r;
+      ck[k] = c;
+      f[k] = 0x7fffffff;
+      rv[k] = 0u;
+      if (r < rows) {
+        const int i = rlo + r, w = wlo + c;
+        const int strip = w < 32 ? 0 : 1 + (w - 32) / 31;
+        int band = (int)((float)i * inv_br);  // then corrected to i / br exactly
+        band -= band * br > i;
+        band += (band + 1) * br <= i;
+        f[k] = __ldcg(j.first33 + (int64_t)band * j.strips + strip);
+        rv[k] = __ldcg(raw + (int64_t)i * pw + w);
+      }
+      r += dr;
+      c += dc;
+      if (c >= BW) {
+        c -= BW;
+        ++r;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k) {
+      if (rk[k] < rows) {
+        const int i = rlo + rk[k], w = wlo + ck[k];
+        const uint32_t v = f[k] <= i ? rv[k] : 0u;
+        out[rk[k] * P + ck[k]] = v;
+        if (v) {
+          rmin = min(rmin, i);
+          rmax = max(rmax, i);
+          wmin = min(wmin, w);
+          wmax = max(wmax, w);
+        }
+      }
+    }
+  }
+  int box[4];
+  fold_box(rmin, rmax, wmin, wmax, part, box);
+  return SP{out, rlo, wlo, P, BW, rows, box[0], box[1], box[2], box[3]};
+}
+
+// From cur = S_a (a = 32 or 33; the two free planes f0, f1 hold rows
+// [rlo, rhi) x words [wlo, whi) at pitch odd_pitch(whi - wlo)): doubling,
+// search, witness, and the key (atomicMax on the job's state) when some S_t
+// with t >= a is non-empty.  `part`: two fold buffers; the caller's last
+// fold used part[1 - par0].
+__device__ __forceinline__ void solve(const Job& j, SP cur, int a, uint32_t* f0, uint32_t* f1,
+                                      int rlo, int rhi, int wlo, int whi, int (*part)[32][4],
+                                      int par0) {
+  __shared__ unsigned long long s_first;
+  if (threadIdx.x == 0) s_first = ~0ull;
+  __syncthreads();
+  int par = par0;
+  const int BW = whi - wlo, P = odd_pitch(BW);
+  const int kmax = (int)min(j.m, j.n);
+  SP nxt{f0, rlo, wlo, P, BW, rhi - rlo, 0, 0, 0, 0};
+  int lo, hi;
+  for (;;) {
+    if (2 * a > kmax || cur.empty()) {
+      lo = a;
+      hi = min(2 * a, kmax + 1);
+      break;
+    }
+    grow_write(cur, nxt, a, part[par]);
+    par ^= 1;
+    if (nxt.empty()) {
+      lo = a;
+      hi = 2 * a;
+      break;
+    }
+    a *= 2;
+    // the levels alternate between f0 and f1 (the starting plane is done with)
+    uint32_t* other = nxt.p == f0 ? f1 : f0;
+    cur = nxt;
+    nxt = SP{other, rlo, wlo, P, BW, rhi - rlo, 0, 0, 0, 0};
+  }
+  if (cur.empty()) return;  // S_a itself empty: nothing above the tiles' own result
+  // search: several sides per pass while the plane is small, else halving
+  const int nw = max(1, (cur.ar1 - cur.ar0) * (cur.aw1 - cur.aw0));
+  const int ways = max(1, min(kWays, kProbeBudget * (int)blockDim.x / nw));
+  while (hi - lo > 1) {
+    const int span = hi - lo;
+    const int T = min(ways, span - 1);
+    const unsigned m = probe(cur, a, lo, span, T, part[par]);
+    par ^= 1;
+    // S_t shrinks as t grows: the set bits are a prefix of the sides tested
+    const int ok = __popc(m & ((1u << T) - 1u));
+    const int nlo = ok ? lo + ok * span / (T + 1) : lo;
+    const int nhi = ok < T ? lo + (ok + 1) * span / (T + 1) : hi;
+    lo = nlo;
+    hi = nhi;
+  }
+  const unsigned long long idx = first_bit(cur, lo - a, j.n, &s_first, j.corners_count ? &j : nullptr);
+  if (threadIdx.x == 0 && idx != ~0ull)
+    atomicMax(&j.st->key, make_key((int32_t)lo, (int64_t)(idx / (unsigned long long)j.n),
+                                   (int64_t)(idx % (unsigned long long)j.n), j.n));
+}
+
+}  // namespace sbox
+
 // Size-only, by a team of `team_size` blocks (ranks 0..team_size-1, all
 // called with the same box; `sync` may be null only for a team of one).  When
 // the three planes fit in `smem_words` words of shared memory, rank 0 works
@@ -1103,13 +1425,33 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
   // bitplane tiles hand over S_33 of the box; else S_32 is built from the
   // input on the box grown by the halo
   const bool from33 = j.first33 != nullptr;
-  const int64_t box_words = (int64_t)(rhi - rlo) * (whi - wlo);
-  const bool fits = smem && (from33 ? 3 * box_words
+  const int64_t box_plane = (int64_t)(rhi - rlo) * sbox::odd_pitch(whi - wlo);
+  const bool fits = smem && (from33 ? 3 * box_plane
                                     : 2 * (int64_t)g.RP * g.Wv + (int64_t)g.R1 * g.W1) <= smem_words;
   // (a cluster's other blocks may leave: rank 0 alone never uses the cluster
   // barrier)
   const bool alone = fits || !sync || team_size <= 1;
   if (alone && rank != 0) return;
+  if (fits) {
+    // one block with every plane in shared memory: the specialised passes
+    if (from33) {
+      const sbox::SP s33 = sbox::gather33(j, rlo, rhi, wlo, whi, smem, s_part[0]);
+      sbox::solve(j, s33, kHalo + 1, smem + box_plane, smem + 2 * box_plane, rlo, rhi, wlo, whi,
+                  s_part, 1);
+    } else {
+      Team t1{1, 0, nullptr, &j.st->status, 0u, false, false};
+      PassBox pb1{s_part, 0, &t1};
+      uint32_t* in = smem;                             // input bits, then a level plane
+      uint32_t* vb = smem + (int64_t)g.RP * g.Wv;      // V_32, then a level plane
+      uint32_t* s32buf = smem + 2 * (int64_t)g.RP * g.Wv;
+      const Plane s32 = build_s32<FMT>(j, g, in, vb, s32buf, pb1);
+      const sbox::SP cur{s32.p, s32.r0, s32.w0, s32.pitch, s32.pitch, g.R1,
+                         s32.ar0, s32.ar1, s32.aw0, s32.aw1};
+      sbox::solve(j, cur, 32, vb, in, rlo, rhi, wlo, whi, s_part, pb1.k & 1);
+    }
+    __syncthreads();
+    return;
+  }
   Team tm{alone ? 1 : team_size, alone ? 0 : rank, alone ? nullptr : sync, &j.st->status, 0u,
           false, cluster && !alone};
   PassBox pb{s_part, 0, &tm};
@@ -1120,23 +1462,13 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
     }
   }
   unsigned long long* first = alone ? &s_first : &sync->first;
-  uint32_t *buf0, *buf1, *buf2;  // V_32 then levels / S_32 on the grown box / input then levels
-  if (fits && from33) {
-    buf1 = smem;
-    buf0 = smem + box_words;
-    buf2 = smem + 2 * box_words;
-  } else if (fits) {
-    buf2 = smem;
-    buf0 = smem + g.RP * g.Wv;
-    buf1 = smem + 2 * g.RP * g.Wv;
-  } else {
-    // (from33: the tiles' S_33 rows sit in the third plane, free again once
-    // the box's S_33 is gathered into the second)
-    const int64_t cap = j.m * ((j.n + 31) / 32 + 2);
-    buf0 = j.bits_scratch;
-    buf1 = j.bits_scratch + cap;
-    buf2 = j.bits_scratch + 2 * cap;
-  }
+  // planes in the job's global scratch: V_32 then levels / S_32 on the grown
+  // box / input then levels (from33: the tiles' S_33 rows sit in the third
+  // plane, free again once the box's S_33 is gathered into the second)
+  const int64_t cap = j.m * ((j.n + 31) / 32 + 2);
+  uint32_t* buf0 = j.bits_scratch;
+  uint32_t* buf1 = j.bits_scratch + cap;
+  uint32_t* buf2 = j.bits_scratch + 2 * cap;
   const Plane s_a = from33 ? gather_s33(j, rlo, rhi, wlo, whi, buf1, pb)
                            : build_s32<FMT>(j, g, buf2, buf0, buf1, pb);
   // 4. doubling from a = 32 (or 33) inside the box [rlo, rhi) x [wlo, whi),
