@@ -448,12 +448,10 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   const int fuse = ntiles > 0 && ((!DPMAP && j.bits_scratch && j.m * j.n < kFusedFinishCells) ||
                                    (DPMAP && !j.test_hold && j.m * j.n < kFusedFinishCellsDp))
                        ? 1 : 0;
-  // a fix-up cluster after the tile pass: clear its team state now, so that
-  // the fix-up follows the tile kernel directly on the stream
+  // a fix-up cluster after the tile pass: the tile kernel clears its team
+  // state, so that the fix-up follows it directly on the stream
   const int team = fix_team_size(j.m * j.n, std::min(kFixClusterBlocks, ctx->sms));
-  if (!fuse && team > 1 && j.bits_scratch &&
-      cudaMemsetAsync(ctx->d_sync1, 0, sizeof(ms::TeamSync), s) != cudaSuccess)
-    return cudaGetLastError();
+  ms::TeamSync* clear = (!fuse && team > 1 && j.bits_scratch) ? ctx->d_sync1 : nullptr;
   if (ntiles > 0 && !DPMAP && j.tile_kind == 1) {
     // bitplane tiles: one tile per warp
     ProfScope ps(ctx, s, kProfTile);
@@ -464,11 +462,11 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
     if (fuse) {
       if (allow_smem((const void*)ms::k_bitiles_one<FMT, true>, sm) != cudaSuccess)
         return cudaGetLastError();
-      ms::k_bitiles_one<FMT, true><<<grid, 32 * wpb, sm, s>>>(j, ntiles);
+      ms::k_bitiles_one<FMT, true><<<grid, 32 * wpb, sm, s>>>(j, ntiles, clear);
     } else {
       if (allow_smem((const void*)ms::k_bitiles_one<FMT, false>, sm) != cudaSuccess)
         return cudaGetLastError();
-      ms::k_bitiles_one<FMT, false><<<grid, 32 * wpb, sm, s>>>(j, ntiles);
+      ms::k_bitiles_one<FMT, false><<<grid, 32 * wpb, sm, s>>>(j, ntiles, clear);
     }
   } else if (ntiles > 0) {
     ProfScope ps(ctx, s, kProfTile);
@@ -484,7 +482,7 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
   case PP:                                                                              \
     if (allow_smem((const void*)ms::k_tiles_one<PP, FMT, DPMAP>, sm) != cudaSuccess)    \
       return cudaGetLastError();                                                        \
-    ms::k_tiles_one<PP, FMT, DPMAP><<<grid, 32 * wpb, sm, s>>>(j, ntiles, fuse);        \
+    ms::k_tiles_one<PP, FMT, DPMAP><<<grid, 32 * wpb, sm, s>>>(j, ntiles, fuse, clear); \
     break;
       MS_LAUNCH_TILES(1)
       MS_LAUNCH_TILES(2)

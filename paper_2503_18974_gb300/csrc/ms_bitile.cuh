@@ -414,8 +414,10 @@ __device__ __forceinline__ void tile_one(const Job& j, int64_t t) {
 // matrices; the large ones take the variant without that code, whose tile
 // loop then keeps every register to itself).
 template <int FMT, bool FUSE>
-__global__ void __launch_bounds__(256, 3) k_bitiles_one(const Job job, int64_t ntiles) {
+__global__ void __launch_bounds__(256, 3) k_bitiles_one(const Job job, int64_t ntiles,
+                                                         TeamSync* team) {
   grid_dependents_may_launch();
+  clear_team(team);
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (w < ntiles) bt::tile_one<FMT>(job, w);
   if constexpr (FUSE) {

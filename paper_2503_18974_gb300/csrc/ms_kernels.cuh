@@ -701,6 +701,13 @@ struct TeamSync {            // one per matrix, zeroed before the launch
   int box[3][4];             // pass boxes (as PassBox slots)
   unsigned long long first;  // witness: smallest row-major index
 };
+static_assert(sizeof(TeamSync) == 64, "cleared as 16 words");
+
+// Zeroes a single call's team state from the tile kernel before it (the
+// fix-up reads it only after waiting for that grid); null: nothing to clear.
+__device__ __forceinline__ void clear_team(TeamSync* t) {
+  if (t && blockIdx.x == 0 && threadIdx.x < 16) reinterpret_cast<uint32_t*>(t)[threadIdx.x] = 0u;
+}
 struct Team {
   int size, rank;
   TeamSync* sync;  // null when size == 1
@@ -1833,8 +1840,10 @@ __global__ void __launch_bounds__(kFixWarps * 32, 1) k_fixup_one(const Job job, 
 // block's ring memory or the job's scratch; dp map: the strip fix-up over the
 // block's warps), then the result -- so that one launch does the whole call.
 template <int P, int FMT, bool DPMAP>
-__global__ void __launch_bounds__(256, 2) k_tiles_one(const Job job, int64_t ntiles, int fuse) {
+__global__ void __launch_bounds__(256, 2) k_tiles_one(const Job job, int64_t ntiles, int fuse,
+                                                       TeamSync* team) {
   grid_dependents_may_launch();
+  clear_team(team);
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   tile_pass_warp<P, FMT, DPMAP>(&job, 1, ntiles, w);
   if (fuse) {
