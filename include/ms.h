@@ -51,7 +51,8 @@ typedef enum {
   MS_ERR_CUDA = 3,        /* a CUDA runtime call failed */
   MS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up (reported per matrix) */
   MS_ERR_BUDGET = 5,      /* request does not fit the serving memory budget */
-  MS_ERR_UNSUPPORTED = 6  /* valid but outside the supported sizes or layouts */
+  MS_ERR_UNSUPPORTED = 6, /* valid but outside the supported sizes or layouts */
+  MS_ERR_CANCELLED = 7    /* a served request withdrawn by ms_server_cancel */
 } ms_status;
 
 typedef enum {
@@ -136,8 +137,11 @@ ms_status ms_destroy(ms_ctx* ctx);
  * - Limits: m <= 8192 and n <= 8192 (MS_U8 or MS_BITS32); a larger matrix
  *   returns MS_ERR_UNSUPPORTED and launches nothing.
  * - The first call on each device looks up the scratch array's device
- *   address (cudaGetSymbolAddress, with that device current); make that
- *   first call before any stream capture on that device.
+ *   address (cudaGetSymbolAddress, with that device current) and raises the
+ *   kernels' shared-memory limits; make that first call before any stream
+ *   capture on that device.  A call in a new context of the device (after
+ *   cudaDeviceReset) repeats that set-up, so it too should come before any
+ *   capture.
  * - Every call on a device shares the one scratch array and clears the parts
  *   that must start at zero.  Calls whose work overlaps on the GPU (other
  *   streams, other host threads) race on it and give wrong results: order
@@ -201,7 +205,12 @@ typedef struct {
   size_t memory_budget_bytes; /* device memory for resident request inputs */
   int32_t streams;            /* concurrent batches (default 2) */
   int32_t max_batch;          /* requests per batch (default 512) */
-  int32_t reserved[4];
+  /* Test hook for failure handling, 0 in normal use: when k > 0, the k-th
+   * batch the server launches (counting from 1) is treated as a launch that
+   * failed on the host: its requests complete with MS_ERR_CUDA and side 0,
+   * while every other request is served normally. */
+  int32_t test_fail_batch;
+  int32_t reserved[3];
 } ms_server_config;
 
 typedef struct {
@@ -223,6 +232,13 @@ ms_status ms_server_create(ms_server** out, int device, const ms_server_config* 
 ms_status ms_server_submit(ms_server* srv, const ms_matrix* host_matrix, double t_arrival,
                            uint64_t* id);  /* t_arrival < 0: now */
 ms_status ms_server_poll(ms_server* srv, ms_server_completion* out, int32_t max, int32_t* n_out);
+/* Withdraw a request that is still waiting for admission: it completes at
+ * once (its completion is returned by ms_server_poll) with status
+ * MS_ERR_CANCELLED and side 0, and its host matrix is no longer read.
+ * Returns MS_OK, or MS_ERR_INVALID when the id is unknown or the request has
+ * already been admitted (its input is being copied, computed or done: it
+ * then completes normally). */
+ms_status ms_server_cancel(ms_server* srv, uint64_t id);
 ms_status ms_server_wait_all(ms_server* srv);
 ms_status ms_server_stats_get(ms_server* srv, ms_server_stats* out);
 ms_status ms_server_destroy(ms_server* srv);

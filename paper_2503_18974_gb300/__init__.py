@@ -30,7 +30,8 @@ _HEADER = os.path.join(_ROOT, "include", "ms.h")
 MS_U8 = 0
 MS_BITS32 = 1
 STATUS = {0: "MS_OK", 1: "MS_ERR_INVALID", 2: "MS_ERR_OOM", 3: "MS_ERR_CUDA",
-          4: "MS_ERR_TIMEOUT", 5: "MS_ERR_BUDGET", 6: "MS_ERR_UNSUPPORTED"}
+          4: "MS_ERR_TIMEOUT", 5: "MS_ERR_BUDGET", 6: "MS_ERR_UNSUPPORTED",
+          7: "MS_ERR_CANCELLED"}
 
 NVCC_FLAGS = ["-O3", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
               "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "--threads", "4"]
@@ -86,7 +87,8 @@ class _Result(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_size_t), ("streams", ctypes.c_int32),
-                ("max_batch", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("max_batch", ctypes.c_int32), ("test_fail_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class Completion(ctypes.Structure):
@@ -108,7 +110,8 @@ EXPORTS = ("ms_create", "ms_destroy", "ms_max_square", "ms_dp_map", "ms_all_max_
            "ms_max_cube", "ms_batch",
            "ms_status_string", "ms_set_tuning", "ms_get_tuning", "ms_profile_start",
            "ms_profile_stop", "ms_autotune", "ms_max_square_noalloc", "ms_server_create",
-           "ms_server_submit", "ms_server_poll", "ms_server_wait_all", "ms_server_stats_get",
+           "ms_server_submit", "ms_server_poll", "ms_server_cancel", "ms_server_wait_all",
+           "ms_server_stats_get",
            "ms_server_destroy", "ms_server_now")
 
 
@@ -151,6 +154,8 @@ def lib():
                                      ctypes.POINTER(ctypes.c_int32)]
         L.ms_server_wait_all.restype = ctypes.c_int
         L.ms_server_wait_all.argtypes = [vp]
+        L.ms_server_cancel.restype = ctypes.c_int
+        L.ms_server_cancel.argtypes = [vp, ctypes.c_uint64]
         L.ms_server_stats_get.restype = ctypes.c_int
         L.ms_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
         L.ms_server_destroy.restype = ctypes.c_int
@@ -364,8 +369,8 @@ class Server:
     """The libms request server (admission by memory budget, continuous batching)."""
 
     def __init__(self, device: int = 0, memory_budget: int = 16 << 30, streams: int = 2,
-                 max_batch: int = 512):
-        cfg = ServerConfig(memory_budget, streams, max_batch)
+                 max_batch: int = 512, test_fail_batch: int = 0):
+        cfg = ServerConfig(memory_budget, streams, max_batch, test_fail_batch)
         h = ctypes.c_void_p()
         _check(lib().ms_server_create(ctypes.byref(h), device, ctypes.byref(cfg)),
                "ms_server_create")
@@ -406,6 +411,11 @@ class Server:
                         "t_submit": c.t_submit, "t_admit": c.t_admit, "t_launch": c.t_launch,
                         "t_done": c.t_done})
         return out
+
+    def cancel(self, rid: int) -> int:
+        """Withdraw a request still waiting for admission; returns the status
+        code (0: cancelled, 1: unknown or already admitted)."""
+        return lib().ms_server_cancel(self._h, rid)
 
     def wait_all(self) -> None:
         _check(lib().ms_server_wait_all(self._h), "ms_server_wait_all")

@@ -789,6 +789,7 @@ const char* ms_status_string(ms_status st) {
     case MS_ERR_TIMEOUT: return "MS_ERR_TIMEOUT: a bounded device-side wait gave up";
     case MS_ERR_BUDGET: return "MS_ERR_BUDGET: request exceeds the serving memory budget";
     case MS_ERR_UNSUPPORTED: return "MS_ERR_UNSUPPORTED: outside supported sizes or layouts";
+    case MS_ERR_CANCELLED: return "MS_ERR_CANCELLED: request withdrawn before admission";
   }
   return "unknown ms_status";
 }

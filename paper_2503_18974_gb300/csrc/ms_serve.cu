@@ -116,6 +116,7 @@ struct ms_server {
   std::deque<Request*> admitted;  // copy issued, not launched
   std::deque<ms_server_completion> done;
   uint64_t next_id = 1;
+  int64_t launches = 0;           // batch launches attempted (scheduler thread only)
   int64_t outstanding = 0;        // submitted and not completed
   bool stop = false;
   ms_server_stats stats{};
@@ -257,8 +258,11 @@ bool schedule_round(ms_server* s) {
       r->t_launch = t;
       r->t_done = 0;
     }
-    ms_status st = ms_batch(ln.ctx, descs.data(), (int32_t)descs.size(), ln.d_res,
-                            reinterpret_cast<ms_stream_t>(ln.stream));
+    const int64_t ordinal = ++s->launches;
+    ms_status st = (s->cfg.test_fail_batch > 0 && ordinal == s->cfg.test_fail_batch)
+                       ? MS_ERR_CUDA  // test hook: this launch counts as failed
+                       : ms_batch(ln.ctx, descs.data(), (int32_t)descs.size(), ln.d_res,
+                                  reinterpret_cast<ms_stream_t>(ln.stream));
     if (st == MS_OK &&
         cudaMemcpyAsync(ln.h_res, ln.d_res, descs.size() * sizeof(ms_result),
                         cudaMemcpyDeviceToHost, ln.stream) != cudaSuccess)
@@ -396,6 +400,30 @@ ms_status ms_server_poll(ms_server* s, ms_server_completion* out, int32_t max, i
     s->done.pop_front();
   }
   *n_out = n;
+  return MS_OK;
+}
+
+ms_status ms_server_cancel(ms_server* s, uint64_t id) {
+  if (!s) return MS_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = std::find_if(s->pending.begin(), s->pending.end(),
+                           [&](const Request* r) { return r->id == id; });
+    if (it == s->pending.end()) return MS_ERR_INVALID;  // unknown, or admitted already
+    Request* r = *it;
+    s->pending.erase(it);
+    ms_server_completion c;
+    c.id = r->id;
+    c.result = ms_result{0, -1, -1, (int32_t)MS_ERR_CANCELLED};
+    c.t_submit = r->t_submit;
+    c.t_admit = c.t_launch = 0.0;
+    c.t_done = now_s();
+    delete r;  // never admitted: it holds no arena space or event
+    s->done.push_back(c);
+    s->stats.completed++;
+    s->outstanding--;
+  }
+  s->idle_cv.notify_all();
   return MS_OK;
 }
 
