@@ -114,7 +114,11 @@ ms_status ms_all_max_squares(ms_ctx* ctx, const ms_matrix* in, int32_t* corners_
 /* Side and witness for `count` matrices of possibly different shapes and
  * formats in one pass: the descriptors are read from HOST memory (ins_host),
  * the results go to outs_dev[0..count-1] in device memory.  Work from all
- * matrices is scheduled together.  After a first call with a given set of
+ * matrices is scheduled together: by default matrices up to about 900 000
+ * cells are solved whole, one per block, in two persistent launches (their
+ * bitplanes in shared memory), and larger ones as bitplane tiles of one
+ * persistent launch followed by the exact fix-up of their flagged boxes
+ * (see ms_tuning.tile_kind).  After a first call with a given set of
  * shapes, the same call (same pointers, shapes and count) may be captured in
  * a CUDA graph: it then allocates nothing and performs no host-device copy
  * other than stream-ordered ones issued inside the call. */
@@ -256,8 +260,12 @@ double ms_server_now(void);
  * per warp (16-bit lanes), 2 = bitplane tiles (one tile of 1024 columns per
  * warp, 32 cells per word, doubling and threshold tests); automatically
  * bitplane tiles when the matrix fills the GPU's resident tile warps with
- * bands of 64 rows or more.  ms_batch takes bitplane tiles only with
- * tile_kind 2.
+ * bands of 64 rows or more.  For ms_batch, tile_kind 0 solves every matrix
+ * whose two bitplanes fit one block's shared memory (about 28 000 words of
+ * 32 cells each) whole in one block and sends the larger ones through
+ * bitplane tiles and the box fix-up, 1 runs every matrix as dp-recurrence
+ * tile pairs and 2 every matrix as bitplane tiles; ms_autotune chooses among
+ * the three for a batch.
  * 0 for band_rows, lane_cols or tile_kind = choose automatically from the
  * matrix size. */
 typedef struct {

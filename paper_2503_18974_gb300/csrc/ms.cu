@@ -14,6 +14,7 @@
 #include "ms_bitile.cuh"
 #include "ms_bits.cuh"
 #include "ms_kernels.cuh"
+#include "ms_small.cuh"
 
 using ms::Job;
 using ms::JobState;
@@ -37,6 +38,10 @@ struct ms_ctx {
   int64_t first33_cap = 0;
   int64_t bitfix_cap = 0;        // uint32 words
   ms::TeamSync* d_sync1 = nullptr;  // barrier of a single matrix's fix-up team
+  // a second stream for the small matrices of a batch, forked from and
+  // joined back into the caller's stream with two events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
   // batch job table: device copy, the host image it was uploaded from, and a
   // pinned staging buffer guarded by an event
@@ -340,6 +345,17 @@ int fix_team_size(int64_t cells, int cap, int shift = 23) {
 int64_t bitfix_words(const Job& j) { return j.m > 0 && j.n > 0 ? 3 * j.m * ((j.n + 31) / 32 + 2) : 0; }
 constexpr int64_t kBitfixCapWords = (int64_t)1 << 30;  // 4 GiB
 constexpr size_t kBitsFixSmemBytes = 200 * 1024;         // planes of small boxes
+// Batch matrices solved whole in one block, by size class: two planes of at
+// most `words` words each, blocks of `threads` threads, `per_sm` blocks per
+// SM (the kernel keeps 1024 of its threads on an SM).
+struct SmallClass {
+  int64_t words;
+  int threads, per_sm;
+};
+constexpr SmallClass kSmall[4] = {{2048, 128, 8},    // 16 KB
+                                  {6144, 256, 4},    // 48 KB
+                                  {14336, 512, 2},   // 112 KB
+                                  {28672, 1024, 1}};  // 224 KB
 constexpr int kFixClusterBlocks = 8;  // a single large matrix's fix-up cluster (portable size)
 
 
@@ -758,7 +774,7 @@ __global__ void __launch_bounds__(ms::kFixWarps * 32, 1) k_fixup_mixed(const Job
   const int j = blockIdx.x;
   if (j >= njobs) return;
   const Job job = jobs[j];
-  if (job.bits_scratch) return;  // done by k_fixup_bits_mixed
+  if (job.bits_scratch || job.tile_kind == 2) return;  // k_fixup_bits_mixed / the small launch
   if (job.fmt == MS_U8)
     ms::fixup_job<MS_U8, false>(job);
   else
@@ -839,6 +855,13 @@ ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes) {
     delete ctx;
     return MS_ERR_OOM;
   }
+  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    ms_destroy(ctx);
+    return MS_ERR_CUDA;
+  }
   ms_status st = ensure_workspace(ctx, 64, 1 << 16, 1024, nullptr);
   if (st != MS_OK) {
     ms_destroy(ctx);
@@ -865,6 +888,9 @@ ms_status ms_destroy(ms_ctx* ctx) {
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
     if (ctx->d_sync1) cudaFree(ctx->d_sync1);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     for (auto& ps : ctx->prof_pool) {
       cudaEventDestroy(ps.a);
       cudaEventDestroy(ps.b);
@@ -937,44 +963,64 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   DeviceGuard g(ctx->device);
   const bool cap = capturing(s);
 
-  // plan: group tiles by (format, columns per lane) so each group is one launch
+  // Plan.  By default (tile_kind 0) a matrix whose two bitplanes fit one
+  // block's shared memory is solved whole by the small-matrix launch, and the
+  // larger ones go through bitplane tiles and the box fix-up; tile_kind 2
+  // sends every matrix through bitplane tiles, tile_kind 1 (or an explicit
+  // lane width) through tile pairs of the dp recurrence.
   const ms_tuning tune = effective_tuning(ctx, ins_host, count, true);
+  const int mode = tune.lane_cols > 0 ? 1 : tune.tile_kind;
   std::vector<Job> jobs((size_t)count);
-  int64_t carry = 0, progress = 0, work = 0;
-  // batched matrices take bitplane tiles only when the tuning asks for them
-  // (tile_kind 2): inside the persistent launch, whose registers the
-  // dp-recurrence variants size (two blocks of 8 warps per SM), they measured
-  // slower than the dp recurrence's tile pairs (C4: tile pass 0.95 ms
-  // against 0.60 ms), though their fix-up starts from the tiles' S_33
-  const bool bit_all = tune.tile_kind == 2 && tune.lane_cols == 0;
+  std::vector<int32_t> small[4];  // matrices for the small-matrix launches, by class
+  int64_t carry = 0, progress = 0, work_dp = 0, work_bit = 0;
   for (int32_t i = 0; i < count; ++i) {
     jobs[i] = plan_job(tune, &ins_host[i], false, 16, 0);  // dp recurrence: P <= 16
     Job& j = jobs[i];
-    if (bit_all && j.m > 0 && j.n > 0) {
+    const bool empty = j.m <= 0 || j.n <= 0;
+    const int64_t pw = empty ? 0 : ms::small::plane_words(j.m, j.n);
+    if (mode == 0 && pw <= kSmall[3].words) {
+      j.tile_kind = 2;  // solved whole; no tiles, no fix-up state
+      j.strips = j.bands = 0;
+      int c = 0;
+      while (pw > kSmall[c].words) ++c;
+      small[c].push_back(i);
+      continue;
+    }
+    if (mode != 1 && !empty) {
       j.P = 32;
       j.tile_kind = 1;
       j.strips = (int32_t)strips_for(j.n, 32);
+      work_bit += j.m * (int64_t)j.strips;
+    } else {
+      work_dp += j.m * (int64_t)j.strips;
     }
     carry += ms::carry_words(j.m, j.strips_fix);
     progress += j.strips_fix;
-    work += j.m * (int64_t)j.strips;
   }
-  // one band height for the whole batch, sized on the batch's total work
-  const int64_t br = tune.band_rows > 0 ? tune.band_rows : auto_band_rows_for(work);
+  // band heights: dp-recurrence pairs from their total work; bitplane tiles
+  // at least 128 rows (the 32-row halo), else as many as fill the GPU's
+  // resident tile warps once
+  const int64_t br_dp = tune.band_rows > 0 ? tune.band_rows : auto_band_rows_for(work_dp);
+  const int64_t br_bit =
+      tune.band_rows > 0 ? tune.band_rows
+                         : std::min<int64_t>(16384, std::max<int64_t>(
+                               128, (work_bit + ctx->bit_slots - 1) / std::max(1, ctx->bit_slots)));
   for (Job& j : jobs) {
-    if (j.m > 0 && j.n > 0) {
-      j.band_rows = (int32_t)std::min<int64_t>(br, j.m);
-      j.bands = (int32_t)((j.m + j.band_rows - 1) / j.band_rows);
-    }
+    if (j.tile_kind == 2 || j.m <= 0 || j.n <= 0) continue;
+    const int64_t br = j.tile_kind == 1 ? br_bit : br_dp;
+    j.band_rows = (int32_t)std::min<int64_t>(br, j.m);
+    j.bands = (int32_t)((j.m + j.band_rows - 1) / j.band_rows);
   }
-  ms_status st = ensure_workspace(ctx, count, carry, progress, s);
+  ms_status st = ensure_workspace(ctx, count, std::max<int64_t>(carry, 1),
+                                  std::max<int64_t>(progress, 1), s);
   if (st != MS_OK) return st;
-  // tiles of one format and lane width pair up in a warp; pairs of similar
-  // length, longest first, form the queue of the persistent launch
+  // tiles of one format and lane width form a group; dp-recurrence tiles pair
+  // up in a warp, bitplane tiles go one per task; longest first
   struct TileRef { int32_t job, tile, steps; };
   std::vector<std::vector<TileRef>> groups(2 * 64);
   int64_t carry_off = 0, prog_off = 0, bit_need = 0;
-  for (int32_t i = 0; i < count; ++i) bit_need += bitfix_words(jobs[i]);
+  for (int32_t i = 0; i < count; ++i)
+    if (jobs[i].tile_kind != 2) bit_need += bitfix_words(jobs[i]);
   bit_need = std::min(bit_need, kBitfixCapWords);
   if (bit_need > 0 && grow(ctx, ctx->d_bitfix, ctx->bitfix_cap, bit_need, cap) != MS_OK)
     bit_need = 0;
@@ -991,48 +1037,61 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     j.tile0 = 0;
     j.out = outs_dev + i;
     j.st = ctx->d_states + i;
+    j.bits_scratch = nullptr;
+    j.first33 = nullptr;
+    if (j.tile_kind == 2) continue;
     j.carry = ctx->d_carry + carry_off;
     j.progress = ctx->d_progress + prog_off;
     carry_off += ms::carry_words(j.m, j.strips_fix);
     prog_off += j.strips_fix;
     const int64_t bw = bitfix_words(j);
-    j.bits_scratch = nullptr;
     if (bw > 0 && bit_off + bw <= bit_need) {
       j.bits_scratch = ctx->d_bitfix + bit_off;
       bit_off += bw;
     }
     if (j.bits_scratch) any_bits = true; else any_strip = true;
     const int64_t nt = tiles_of(j);
-    j.first33 = nullptr;
     if (j.tile_kind == 1 && j.bits_scratch && f33) {
       j.first33 = ctx->d_first33 + f33_off;
       f33_off += nt;
     }
-    auto& g = groups[j.fmt * 64 + j.P];
-    for (int64_t t = 0; t < nt; ++t) g.push_back(TileRef{i, (int32_t)t, tile_steps(j, t)});
+    auto& grp = groups[j.fmt * 64 + j.P];
+    for (int64_t t = 0; t < nt; ++t) grp.push_back(TileRef{i, (int32_t)t, tile_steps(j, t)});
   }
-  std::vector<ms::PairTask> tasks;
+  std::vector<ms::PairTask> tasks, bit_tasks;
   std::vector<int> task_steps;
-  for (auto& g : groups) {
-    std::stable_sort(g.begin(), g.end(),
-                     [](const TileRef& a, const TileRef& b) { return a.steps > b.steps; });
-    // (bitplane tiles, lane width 32, go one per task)
-    const size_t stride = (!g.empty() && jobs[g[0].job].tile_kind == 1) ? 1 : 2;
-    for (size_t k = 0; k < g.size(); k += stride) {
+  for (auto& grp : groups) {
+    std::stable_sort(grp.begin(), grp.end(),
+                     [](const TileRef& x, const TileRef& y) { return x.steps > y.steps; });
+    if (!grp.empty() && jobs[grp[0].job].tile_kind == 1) {
+      for (const TileRef& r : grp) bit_tasks.push_back(ms::PairTask{r.job, -1, r.tile, 0});
+      continue;
+    }
+    for (size_t k = 0; k < grp.size(); k += 2) {
       ms::PairTask t;
-      t.job_a = g[k].job;
-      t.tile_a = g[k].tile;
-      t.job_b = stride == 2 && k + 1 < g.size() ? g[k + 1].job : -1;
-      t.tile_b = stride == 2 && k + 1 < g.size() ? g[k + 1].tile : 0;
+      t.job_a = grp[k].job;
+      t.tile_a = grp[k].tile;
+      t.job_b = k + 1 < grp.size() ? grp[k + 1].job : -1;
+      t.tile_b = k + 1 < grp.size() ? grp[k + 1].tile : 0;
       tasks.push_back(t);
-      task_steps.push_back(g[k].steps);
+      task_steps.push_back(grp[k].steps);
     }
   }
+  // bitplane tiles: one launch per input format (uint8 tiles first), longest
+  // first within each
+  std::stable_sort(bit_tasks.begin(), bit_tasks.end(), [&](const ms::PairTask& x,
+                                                           const ms::PairTask& y) {
+    const Job &jx = jobs[x.job_a], &jy = jobs[y.job_a];
+    if (jx.fmt != jy.fmt) return jx.fmt < jy.fmt;
+    return tile_steps(jx, x.tile_a) > tile_steps(jy, y.tile_a);
+  });
+  int nbit_u8 = 0;
+  while (nbit_u8 < (int)bit_tasks.size() && jobs[bit_tasks[nbit_u8].job_a].fmt == MS_U8) ++nbit_u8;
   {
-    // groups stay contiguous in the queue (warps running at the same time
-    // mostly execute one lane-width variant, which keeps the instruction
-    // cache warm), the group with the longest tiles first, longest first
-    // within each group
+    // dp-recurrence groups stay contiguous in the queue (warps running at the
+    // same time mostly execute one lane-width variant, which keeps the
+    // instruction cache warm), the group with the longest tiles first,
+    // longest first within each group
     std::vector<size_t> idx(tasks.size());
     for (size_t k = 0; k < idx.size(); ++k) idx[k] = k;
     std::vector<int> group_of(tasks.size()), group_max(2 * 64, 0);
@@ -1041,29 +1100,34 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
       group_of[k] = ja.fmt * 64 + ja.P;
       group_max[group_of[k]] = std::max(group_max[group_of[k]], task_steps[k]);
     }
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
-      const int ga = group_of[a], gb = group_of[b];
-      if (ga != gb)
-        return group_max[ga] != group_max[gb] ? group_max[ga] > group_max[gb] : ga > gb;
-      return task_steps[a] > task_steps[b];
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+      const int gx = group_of[x], gy = group_of[y];
+      if (gx != gy)
+        return group_max[gx] != group_max[gy] ? group_max[gx] > group_max[gy] : gx > gy;
+      return task_steps[x] > task_steps[y];
     });
     std::vector<ms::PairTask> sorted(tasks.size());
     for (size_t k = 0; k < idx.size(); ++k) sorted[k] = tasks[idx[k]];
     tasks.swap(sorted);
   }
-  const int ntasks = (int)tasks.size();
+  const int ntasks = (int)tasks.size(), nbit = (int)bit_tasks.size();
+  // small matrices largest first within each class
+  auto by_cells = [&](int32_t x, int32_t y) { return jobs[x].m * jobs[x].n > jobs[y].m * jobs[y].n; };
+  int nsmall = 0;
+  for (auto& c : small) {
+    std::stable_sort(c.begin(), c.end(), by_cells);
+    nsmall += (int)c.size();
+  }
 
-  // size-only fix-up blocks: a team per matrix with bitplane scratch, sized by
-  // the matrix, larger teams (then larger matrices) first so that the longest
-  // fix-ups start early
+  // size-only fix-up blocks: a team per tiled matrix with bitplane scratch,
+  // sized by the matrix, larger teams (then larger matrices) first so that
+  // the longest fix-ups start early
   std::vector<ms::FixTask> fix;
   {
     std::vector<int32_t> order;
     for (int32_t i = 0; i < count; ++i)
       if (jobs[i].bits_scratch && jobs[i].m > 0 && jobs[i].n > 0) order.push_back(i);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-      return jobs[a].m * jobs[a].n > jobs[b].m * jobs[b].n;
-    });
+    std::stable_sort(order.begin(), order.end(), by_cells);
     for (int32_t i : order) {
       const int size = fix_team_size(jobs[i].m * jobs[i].n, 16, 18);
       for (int r = 0; r < size; ++r) fix.push_back(ms::FixTask{i, r, size, 0});
@@ -1071,17 +1135,31 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   }
   const int nfix = (int)fix.size();
 
-  // table image: [jobs | tasks | fix tasks | queue counter | team barriers],
-  // 16-byte aligned sections; the last two are cleared before every launch
-  const size_t jobs_bytes = ((size_t)count * sizeof(Job) + 15) / 16 * 16;
-  const size_t tasks_bytes = ((size_t)ntasks * sizeof(ms::PairTask) + 15) / 16 * 16;
-  const size_t fix_bytes = (size_t)nfix * sizeof(ms::FixTask);
-  const size_t clear_bytes = 16 + (size_t)count * sizeof(ms::TeamSync);
-  const size_t table_bytes = jobs_bytes + tasks_bytes + fix_bytes + clear_bytes;
+  // table image: [jobs | tasks | bitplane tasks | fix tasks | small order |
+  // 8 queue counters | team barriers], 16-byte aligned sections; the last two
+  // are cleared before every launch
+  auto a16 = [](size_t x) { return (x + 15) / 16 * 16; };
+  const size_t jobs_bytes = a16((size_t)count * sizeof(Job));
+  const size_t tasks_bytes = a16((size_t)ntasks * sizeof(ms::PairTask));
+  const size_t bit_bytes = a16((size_t)nbit * sizeof(ms::PairTask));
+  const size_t fix_bytes = a16((size_t)nfix * sizeof(ms::FixTask));
+  const size_t order_bytes = a16((size_t)nsmall * sizeof(int32_t));
+  const size_t clear_bytes = 32 + (size_t)count * sizeof(ms::TeamSync);
+  const size_t o_tasks = jobs_bytes, o_bit = o_tasks + tasks_bytes, o_fix = o_bit + bit_bytes,
+               o_order = o_fix + fix_bytes, o_clear = o_order + order_bytes;
+  const size_t table_bytes = o_clear + clear_bytes;
   std::vector<unsigned char> image(table_bytes, 0);
   std::memcpy(image.data(), jobs.data(), (size_t)count * sizeof(Job));
-  if (ntasks) std::memcpy(image.data() + jobs_bytes, tasks.data(), (size_t)ntasks * sizeof(ms::PairTask));
-  if (nfix) std::memcpy(image.data() + jobs_bytes + tasks_bytes, fix.data(), fix_bytes);
+  if (ntasks) std::memcpy(image.data() + o_tasks, tasks.data(), (size_t)ntasks * sizeof(ms::PairTask));
+  if (nbit) std::memcpy(image.data() + o_bit, bit_tasks.data(), (size_t)nbit * sizeof(ms::PairTask));
+  if (nfix) std::memcpy(image.data() + o_fix, fix.data(), (size_t)nfix * sizeof(ms::FixTask));
+  {
+    size_t off = o_order;
+    for (const auto& c : small) {
+      if (!c.empty()) std::memcpy(image.data() + off, c.data(), c.size() * sizeof(int32_t));
+      off += c.size() * sizeof(int32_t);
+    }
+  }
 
   // upload only when it differs from the table already on the device
   if (ctx->uploaded != image) {
@@ -1108,46 +1186,117 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     ctx->uploaded.swap(image);
   }
   const Job* d_jobs = reinterpret_cast<const Job*>(ctx->d_table);
-  const ms::PairTask* d_tasks = reinterpret_cast<const ms::PairTask*>(ctx->d_table + jobs_bytes);
-  const ms::FixTask* d_fix =
-      reinterpret_cast<const ms::FixTask*>(ctx->d_table + jobs_bytes + tasks_bytes);
-  unsigned char* d_clear = ctx->d_table + jobs_bytes + tasks_bytes + fix_bytes;
-  int* d_queue = reinterpret_cast<int*>(d_clear);
-  ms::TeamSync* d_syncs = reinterpret_cast<ms::TeamSync*>(d_clear + 16);
+  const ms::PairTask* d_tasks = reinterpret_cast<const ms::PairTask*>(ctx->d_table + o_tasks);
+  const ms::PairTask* d_bit = reinterpret_cast<const ms::PairTask*>(ctx->d_table + o_bit);
+  const ms::FixTask* d_fix = reinterpret_cast<const ms::FixTask*>(ctx->d_table + o_fix);
+  const int32_t* d_order = reinterpret_cast<const int32_t*>(ctx->d_table + o_order);
+  unsigned char* d_clear = ctx->d_table + o_clear;
+  // queue counters: tile pairs, uint8 and packed bitplane tiles, four small
+  // classes
+  int* d_queues = reinterpret_cast<int*>(d_clear);
+  ms::TeamSync* d_syncs = reinterpret_cast<ms::TeamSync*>(d_clear + 32);
   if (cudaMemsetAsync(d_clear, 0, clear_bytes, s) != cudaSuccess) return MS_ERR_CUDA;
 
-  if (ntasks > 0) {
-    const size_t sm = ring_bytes(kTileThreads);
-    if (allow_smem((const void*)ms::k_batch_tiles, sm) != cudaSuccess) return MS_ERR_CUDA;
-    if (ctx->batch_grid == 0) {
-      int per_sm = 0, sms = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms::k_batch_tiles, kTileThreads,
-                                                        sm) != cudaSuccess ||
-          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
-              cudaSuccess)
-        return MS_ERR_CUDA;
-      ctx->batch_grid = std::max(1, per_sm) * sms;
+  // The small matrices run on the context's second stream, forked from the
+  // caller's after the clear and joined back at the end, so that they share
+  // the GPU with the large matrices' tiles and fix-up (while kernels are
+  // timed by ms_profile_*, everything stays on the caller's stream).
+  const bool fork = nsmall > 0 && (nbit > 0 || ntasks > 0) && !ctx->prof_on;
+  cudaStream_t ss = s;
+  // joins the second stream back on every way out once it is forked (a
+  // capture must not end with a branch left open)
+  struct Join {
+    ms_ctx* c;
+    cudaStream_t s;
+    bool on = false;
+    ~Join() {
+      if (on) {
+        cudaEventRecord(c->ev_join, c->side);
+        cudaStreamWaitEvent(s, c->ev_join, 0);
+      }
     }
-    const int wpb = kTileThreads / 32;
-    const int grid = std::max(1, std::min(ctx->batch_grid, (ntasks + wpb - 1) / wpb));
+  } join{ctx, s};
+  if (fork) {
+    if (cudaEventRecord(ctx->ev_fork, s) != cudaSuccess ||
+        cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0) != cudaSuccess)
+      return MS_ERR_CUDA;
+    join.on = true;
+    ss = ctx->side;
+  }
+  {
     ProfScope ps(ctx, s, kProfTile);
-    ms::k_batch_tiles<<<grid, kTileThreads, sm, s>>>(d_jobs, d_tasks, ntasks, d_queue);
-    if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
+    // large matrices first: bitplane tiles (one launch per input format)
+    for (int k = 0; k < 2; ++k) {
+      const int n = k == 0 ? nbit_u8 : nbit - nbit_u8;
+      if (n == 0) continue;
+      if (ctx->prof_on) ctx->prof_bit++;
+      const size_t sm = (size_t)ms::bt::kWarps * ms::bt::kWarpBytes;
+      const void* fn = k == 0 ? (const void*)ms::k_batch_bitiles<MS_U8>
+                              : (const void*)ms::k_batch_bitiles<MS_BITS32>;
+      if (allow_smem(fn, sm) != cudaSuccess) return MS_ERR_CUDA;
+      const int grid = std::max(1, std::min(ctx->bit_slots / ms::bt::kWarps,
+                                            (n + ms::bt::kWarps - 1) / ms::bt::kWarps));
+      if (k == 0)
+        ms::k_batch_bitiles<MS_U8><<<grid, 32 * ms::bt::kWarps, sm, s>>>(d_jobs, d_bit, n,
+                                                                         d_queues + 1);
+      else
+        ms::k_batch_bitiles<MS_BITS32><<<grid, 32 * ms::bt::kWarps, sm, s>>>(
+            d_jobs, d_bit + nbit_u8, n, d_queues + 2);
+      if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
+    }
+    if (ntasks > 0) {
+      const size_t sm = ring_bytes(kTileThreads);
+      if (allow_smem((const void*)ms::k_batch_tiles, sm) != cudaSuccess) return MS_ERR_CUDA;
+      if (ctx->batch_grid == 0) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ms::k_batch_tiles,
+                                                          kTileThreads, sm) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
+                cudaSuccess)
+          return MS_ERR_CUDA;
+        ctx->batch_grid = std::max(1, per_sm) * sms;
+      }
+      const int wpb = kTileThreads / 32;
+      const int grid = std::max(1, std::min(ctx->batch_grid, (ntasks + wpb - 1) / wpb));
+      ms::k_batch_tiles<<<grid, kTileThreads, sm, s>>>(d_jobs, d_tasks, ntasks, d_queues);
+      if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
+    }
+    // small matrices solved whole, the largest class first
+    int off[4], o = 0;
+    for (int c = 0; c < 4; ++c) {
+      off[c] = o;
+      o += (int)small[c].size();
+    }
+    for (int c = 3; c >= 0; --c) {
+      const int n = (int)small[c].size();
+      if (n == 0) continue;
+      const size_t sm = 2 * (size_t)kSmall[c].words * 4;
+      if (allow_smem((const void*)ms::k_batch_small, sm) != cudaSuccess) return MS_ERR_CUDA;
+      const int grid = std::min(n, kSmall[c].per_sm * ctx->sms);
+      ms::k_batch_small<<<grid, kSmall[c].threads, sm, ss>>>(d_jobs, d_order + off[c], n,
+                                                             d_queues + 3 + c);
+      if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
+    }
   }
   {
     ProfScope ps(ctx, s, kProfFixup);
-    if (any_bits) {
+    if (any_bits && nfix > 0) {
       const size_t smb = kBitsFixSmemBytes / 2;  // two blocks per SM
       if (allow_smem((const void*)ms::k_fixup_bits_mixed, smb) != cudaSuccess) return MS_ERR_CUDA;
-      if (nfix > 0)
-        ms::k_fixup_bits_mixed<<<nfix, ms::kBitsMixedThreads, smb, s>>>(d_jobs, d_fix, d_syncs,
-                                                                        (int64_t)(smb / 4));
+      ms::k_fixup_bits_mixed<<<nfix, ms::kBitsMixedThreads, smb, s>>>(d_jobs, d_fix, d_syncs,
+                                                                      (int64_t)(smb / 4));
     }
     if (any_strip) {
       const size_t smf = ring_bytes(ms::kFixWarps * 32);
       if (allow_smem((const void*)k_fixup_mixed, smf) != cudaSuccess) return MS_ERR_CUDA;
       k_fixup_mixed<<<count, ms::kFixWarps * 32, smf, s>>>(d_jobs, count);
     }
+  }
+  if (join.on) {
+    join.on = false;
+    if (cudaEventRecord(ctx->ev_join, ctx->side) != cudaSuccess ||
+        cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess)
+      return MS_ERR_CUDA;
   }
   return cuda_status(cudaGetLastError());
 }
@@ -1167,19 +1316,24 @@ ms_status ms_autotune(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_
   std::vector<ms_tuning> cands;
   const int rows[] = {0, 32, 64, 128, 256, 512, 1024};
   const int lanes[] = {0, 2, 4, 8, 16, 32};
-  for (int pp = 0; pp <= (packed_single ? 1 : 0); ++pp)
-    for (int lc : lanes)
-      for (int r : rows) {
-        // the bitplane search has no band height or lane width; batches use
-        // the automatic lane width (at most 16)
-        if (pp == 1 && (r != 0 || lc != 0)) continue;
-        if (batch && lc != 0) continue;
-        ms_tuning t{};
-        t.band_rows = r;
-        t.packed_path = pp;
-        t.lane_cols = lc;
-        cands.push_back(t);
-      }
+  // batches also choose how their matrices are tiled: small ones whole and
+  // large ones as bitplane tiles (0), everything as dp-recurrence tile pairs
+  // (1) or everything as bitplane tiles (2)
+  for (int tk = 0; tk <= (batch ? 2 : 0); ++tk)
+    for (int pp = 0; pp <= (packed_single ? 1 : 0); ++pp)
+      for (int lc : lanes)
+        for (int r : rows) {
+          // the bitplane search has no band height or lane width; batches use
+          // the automatic lane width (at most 16)
+          if (pp == 1 && (r != 0 || lc != 0)) continue;
+          if (batch && lc != 0) continue;
+          ms_tuning t{};
+          t.band_rows = r;
+          t.packed_path = pp;
+          t.lane_cols = lc;
+          t.tile_kind = tk;
+          cands.push_back(t);
+        }
   const ms_tuning saved = ctx->tuning;
   const auto saved_cache = ctx->tuned;
   ctx->tuned.clear();

@@ -437,6 +437,26 @@ __global__ void __launch_bounds__(256, 3) k_bitiles_one(const Job job, int64_t n
   }
 }
 
+// ---- batch: bitplane tiles of many matrices, one persistent launch ---------
+//
+// Warps take tiles (task.job_a, task.tile_a) of one input format from the
+// queue, longest first; three blocks of eight warps per SM, as for a single
+// large matrix.
+template <int FMT>
+__global__ void __launch_bounds__(256, 3) k_batch_bitiles(const Job* __restrict__ jobs,
+                                                          const PairTask* __restrict__ tasks,
+                                                          int ntasks, int* queue) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(queue, 1);
+    t = __shfl_sync(kFull, t, 0);
+    if (t >= ntasks) break;
+    const PairTask task = tasks[t];
+    bt::tile_one<FMT>(jobs[task.job_a], task.tile_a);
+  }
+}
+
 // ---- batch: one persistent launch over a queue of tasks -------------------
 //
 // Warps take tasks from an atomic queue until it runs dry: tile pairs of one

@@ -1148,6 +1148,9 @@ struct Runs {
 // (i-d, col-d) for the words' 32 columns, reads left of or above L's active
 // box being zeros.  g(w, v) receives each word in order; the shifted reads of
 // one word are reused by the next.
+// A word whose own bit of L is clear everywhere yields zero without the
+// other reads (the levels of random matrices turn sparse within a few
+// doublings); a run of set words reuses the previous word's shifted reads.
 template <class G>
 __device__ __forceinline__ void grow_run(const SP& L, int i, int wb, int we, int d, G&& g) {
   if (i - d < L.ar0) {  // the square's top row lies above every set bit
@@ -1157,16 +1160,29 @@ __device__ __forceinline__ void grow_run(const SP& L, int i, int wb, int we, int
   const int q = d >> 5, r = d & 31;
   const uint32_t* __restrict__ p = L.p;
   const int bi = L.base(i), bu = L.base(i - d);
+  uint32_t pb = 0u, pc = 0u;
+  bool have = false;  // pb, pc hold the shifted reads of word w - 1
   int wq = wb - q;
-  uint32_t pb = wq - 1 >= L.aw0 ? p[bi + wq - 1] : 0u;
-  uint32_t pc = wq - 1 >= L.aw0 ? p[bu + wq - 1] : 0u;
+#pragma unroll 2
   for (int w = wb; w < we; ++w, ++wq) {
+    const uint32_t a0 = p[bi + w];
+    if (a0 == 0u) {
+      have = false;
+      g(w, 0u);
+      continue;
+    }
+    if (!have) {
+      const bool ok1 = wq - 1 >= L.aw0;
+      pb = ok1 ? p[bi + wq - 1] : 0u;
+      pc = ok1 ? p[bu + wq - 1] : 0u;
+    }
     const bool ok = wq >= L.aw0;
     const uint32_t b = ok ? p[bi + wq] : 0u;
     const uint32_t c = ok ? p[bu + wq] : 0u;
-    g(w, p[bi + w] & p[bu + w] & __funnelshift_l(pb, b, r) & __funnelshift_l(pc, c, r));
+    g(w, a0 & p[bu + w] & __funnelshift_l(pb, b, r) & __funnelshift_l(pc, c, r));
     pb = b;
     pc = c;
+    have = true;
   }
 }
 
@@ -1357,14 +1373,22 @@ __device__ __forceinline__ SP gather33(const Job& j, int rlo, int rhi, int wlo, 
   return SP{out, rlo, wlo, P, BW, rows, box[0], box[1], box[2], box[3]};
 }
 
-// From cur = S_a (a = 32 or 33; the two free planes f0, f1 hold rows
-// [rlo, rhi) x words [wlo, whi) at pitch odd_pitch(whi - wlo)): doubling,
-// search, witness, and the key (atomicMax on the job's state) when some S_t
-// with t >= a is non-empty.  `part`: two fold buffers; the caller's last
-// fold used part[1 - par0].
-__device__ __forceinline__ void solve(const Job& j, SP cur, int a, uint32_t* f0, uint32_t* f1,
-                                      int rlo, int rhi, int wlo, int whi, int (*part)[32][4],
-                                      int par0) {
+// The largest side found from some S_a and the row-major index (i*n + col)
+// of its first corner (side 0: S_a was empty).
+struct Found {
+  int side;
+  unsigned long long idx;
+};
+
+// From cur = S_a: doubling, search and witness.  The level planes alternate
+// between f0 and f1, which hold rows [rlo, rhi) x words [wlo, whi) at pitch
+// odd_pitch(whi - wlo); f1 may be cur's own buffer when cur has that
+// geometry (it is free once the first level is built).  `part`: two fold
+// buffers; the caller's last fold used part[1 - par0].  Every thread
+// returns the same result.
+__device__ __forceinline__ Found solve(const Job& j, SP cur, int a, uint32_t* f0, uint32_t* f1,
+                                       int rlo, int rhi, int wlo, int whi, int (*part)[32][4],
+                                       int par0) {
   __shared__ unsigned long long s_first;
   if (threadIdx.x == 0) s_first = ~0ull;
   __syncthreads();
@@ -1392,7 +1416,7 @@ __device__ __forceinline__ void solve(const Job& j, SP cur, int a, uint32_t* f0,
     cur = nxt;
     nxt = SP{other, rlo, wlo, P, BW, rhi - rlo, 0, 0, 0, 0};
   }
-  if (cur.empty()) return;  // S_a itself empty: nothing above the tiles' own result
+  if (cur.empty()) return Found{0, ~0ull};  // S_a itself empty
   // search: several sides per pass while the plane is small, else halving
   const int nw = max(1, (cur.ar1 - cur.ar0) * (cur.aw1 - cur.aw0));
   const int ways = max(1, min(kWays, kProbeBudget * (int)blockDim.x / nw));
@@ -1409,9 +1433,14 @@ __device__ __forceinline__ void solve(const Job& j, SP cur, int a, uint32_t* f0,
     hi = nhi;
   }
   const unsigned long long idx = first_bit(cur, lo - a, j.n, &s_first, j.corners_count ? &j : nullptr);
-  if (threadIdx.x == 0 && idx != ~0ull)
-    atomicMax(&j.st->key, make_key((int32_t)lo, (int64_t)(idx / (unsigned long long)j.n),
-                                   (int64_t)(idx % (unsigned long long)j.n), j.n));
+  return Found{idx == ~0ull ? 0 : lo, idx};
+}
+
+// Folds a found side and corner into the matrix's key (one thread).
+__device__ __forceinline__ void publish(const Job& j, const Found& f) {
+  if (threadIdx.x == 0 && f.side > 0)
+    atomicMax(&j.st->key, make_key((int32_t)f.side, (int64_t)(f.idx / (unsigned long long)j.n),
+                                   (int64_t)(f.idx % (unsigned long long)j.n), j.n));
 }
 
 }  // namespace sbox
@@ -1443,8 +1472,8 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
     // one block with every plane in shared memory: the specialised passes
     if (from33) {
       const sbox::SP s33 = sbox::gather33(j, rlo, rhi, wlo, whi, smem, s_part[0]);
-      sbox::solve(j, s33, kHalo + 1, smem + box_plane, smem + 2 * box_plane, rlo, rhi, wlo, whi,
-                  s_part, 1);
+      sbox::publish(j, sbox::solve(j, s33, kHalo + 1, smem + box_plane, smem + 2 * box_plane,
+                                   rlo, rhi, wlo, whi, s_part, 1));
     } else {
       Team t1{1, 0, nullptr, &j.st->status, 0u, false, false};
       PassBox pb1{s_part, 0, &t1};
@@ -1454,7 +1483,7 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
       const Plane s32 = build_s32<FMT>(j, g, in, vb, s32buf, pb1);
       const sbox::SP cur{s32.p, s32.r0, s32.w0, s32.pitch, s32.pitch, g.R1,
                          s32.ar0, s32.ar1, s32.aw0, s32.aw1};
-      sbox::solve(j, cur, 32, vb, in, rlo, rhi, wlo, whi, s_part, pb1.k & 1);
+      sbox::publish(j, sbox::solve(j, cur, 32, vb, in, rlo, rhi, wlo, whi, s_part, pb1.k & 1));
     }
     __syncthreads();
     return;
