@@ -298,7 +298,8 @@ def profile_traffic(kernel_key):
         return None
     m = re.search(r"sources_sha1:\s*([0-9a-f]{40})", text)
     h = hashlib.sha1()
-    for f in ("ms.cu", "ms_kernels.cuh", "ms_device.cuh", "ms_bits.cuh", "ms_bitile.cuh"):
+    for f in ("ms.cu", "ms_kernels.cuh", "ms_device.cuh", "ms_bits.cuh", "ms_bitile.cuh",
+              "ms_small.cuh"):
         p = os.path.join(ROOT, "paper_2503_18974_gb300", "csrc", f)
         if os.path.exists(p):
             h.update(open(p, "rb").read())
@@ -501,11 +502,15 @@ def timed(fn, steps, stream, flush=None):
     return sum(a.elapsed_time(b) for a, b in evs)
 
 
-def kernel_label(prof, batch):
+def kernel_label(prof, batch, tile_kind=0):
     if prof.other_ms > prof.tile_ms:
         return "k_bits_search (bitplane doubling + binary search)"
     if batch:
-        return "k_batch_tiles (persistent tile queue)"
+        return {1: "k_batch_tiles (dp-recurrence tile pairs, persistent queue)",
+                2: "k_batch_bitiles (bitplane tiles of every matrix, persistent queue)"}.get(
+            tile_kind, "k_batch_small + k_batch_bitiles (small matrices solved whole in "
+                       "shared memory, large ones as bitplane tiles; one event pair around "
+                       "both)")
     if prof.bit_tile_launches == prof.tile_launches:
         return "k_bitiles_one (bitplane tile pass)"
     if prof.bit_tile_launches == 0:
@@ -630,7 +635,10 @@ def _measure(args, ms, ctx, name, device, stream, pg, clocks, e2e, steps):
                 "peak_source": ("of measured (MEASURED_PEAKS.json hbm_gbs)"
                                 if peak_kind == "measured" else "of fallback 6800 GB/s"),
                 "traffic": (traffic * per_launch_cells if traffic is not None else None),
-                "kernel": kernel_label(prof, batch_label), "bytes_per_cell": wl.bytes_per_cell,
+                "kernel": kernel_label(prof, batch_label,
+                                       (tuned or {}).get("tile_kind", 0) if not args.tile_kind
+                                       else args.tile_kind),
+                "bytes_per_cell": wl.bytes_per_cell,
                 "launches_per_step": kern_launches / steps,
                 "kernel_ms_per_step": kern_ms / steps,
                 "step_achieved": step_achieved, "step_frac": step_achieved / peak,
