@@ -80,6 +80,8 @@ size_t input_bytes(const ms_matrix& m) {
 struct Request {
   uint64_t id;
   ms_matrix host;  // caller's host matrix
+  const void* host_dev = nullptr;  // the same memory's device address when the GPU can
+                                   // read it directly (pinned, mapped), else null
   ms_matrix dev;   // resident copy
   size_t off = 0, bytes = 0;
   double t_submit = 0, t_admit = 0, t_launch = 0, t_done = 0;
@@ -87,6 +89,44 @@ struct Request {
   cudaEvent_t round_done = nullptr;  // the copy round's event (owned by its last request)
   ms_result result{};
 };
+
+// Gather copy of admitted inputs: the GPU reads each request's rows straight
+// from pinned (mapped) host memory into its arena slot, so that a round of
+// admissions costs a few kernel launches instead of one host call per
+// request.  Descriptors travel as kernel parameters.
+struct CopyDesc {
+  const unsigned char* src;  // device address of the host rows
+  unsigned char* dst;
+  int64_t rows;
+  int32_t row_bytes, src_ld, dst_ld, blocks;  // strides in bytes; blocks sharing it
+};
+constexpr int kCopyDescs = 48;  // per launch (the parameters stay below 4 KB)
+struct CopyBatch {
+  CopyDesc d[kCopyDescs];
+  int32_t n;
+};
+static_assert(sizeof(CopyBatch) <= 4000, "kernel parameter size");
+
+__global__ void k_gather_copy(const CopyBatch b) {
+  const int k = blockIdx.y;
+  if (k >= b.n) return;
+  const CopyDesc c = b.d[k];
+  if ((int)blockIdx.x >= c.blocks) return;
+  // 4-byte words when every address and stride allows, else bytes
+  const bool words = ((reinterpret_cast<uintptr_t>(c.src) | reinterpret_cast<uintptr_t>(c.dst) |
+                       (uintptr_t)c.row_bytes | (uintptr_t)c.src_ld | (uintptr_t)c.dst_ld) & 3u) == 0;
+  const int64_t per_row = words ? c.row_bytes / 4 : c.row_bytes;
+  const int64_t total = c.rows * per_row;
+  const int64_t stride = (int64_t)c.blocks * blockDim.x;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+    const int64_t r = t / per_row, e = t - r * per_row;
+    if (words)
+      *reinterpret_cast<uint32_t*>(c.dst + r * c.dst_ld + 4 * e) =
+          *reinterpret_cast<const uint32_t*>(c.src + r * c.src_ld + 4 * e);
+    else
+      c.dst[r * c.dst_ld + e] = c.src[r * c.src_ld + e];
+  }
+}
 
 struct Lane {  // one compute stream with its context and result buffers
   cudaStream_t stream = nullptr;
@@ -208,6 +248,15 @@ bool schedule_round(ms_server* s) {
   // rows are already packed like the device rows, one event per round
   if (!newly.empty()) {
     const double t0 = now_s();
+    CopyBatch cb;
+    cb.n = 0;
+    auto flush = [&]() {
+      if (cb.n == 0) return;
+      int most = 1;
+      for (int k = 0; k < cb.n; ++k) most = std::max(most, cb.d[k].blocks);
+      k_gather_copy<<<dim3((unsigned)most, (unsigned)cb.n), 256, 0, s->copy_stream>>>(cb);
+      cb.n = 0;
+    };
     for (Request* r : newly) {
       const ms_matrix& h = r->host;
       const size_t elem = h.fmt == MS_U8 ? 1 : 4;
@@ -216,16 +265,28 @@ bool schedule_round(ms_server* s) {
       r->dev = h;
       r->dev.data = s->d_arena + r->off;
       r->dev.ld = (int64_t)(dld_bytes / elem);
-      if (h.m > 0 && row > 0) {
-        if ((size_t)h.ld * elem == dld_bytes)
-          cudaMemcpyAsync(s->d_arena + r->off, h.data, dld_bytes * (size_t)h.m,
+      if (h.m <= 0 || row <= 0) continue;
+      const size_t row_bytes = (size_t)row * elem, src_ld = (size_t)h.ld * elem;
+      if (r->host_dev && row_bytes < (1u << 30) && src_ld < (1u << 30)) {
+        CopyDesc& d = cb.d[cb.n++];
+        d.src = static_cast<const unsigned char*>(r->host_dev);
+        d.dst = s->d_arena + r->off;
+        d.rows = h.m;
+        d.row_bytes = (int32_t)row_bytes;
+        d.src_ld = (int32_t)src_ld;
+        d.dst_ld = (int32_t)dld_bytes;
+        // about 64 KB per block, at most 64 blocks per request
+        d.blocks = (int32_t)std::min<int64_t>(64, std::max<int64_t>(1, (h.m * (int64_t)row_bytes) >> 16));
+        if (cb.n == kCopyDescs) flush();
+      } else if (src_ld == dld_bytes) {
+        cudaMemcpyAsync(s->d_arena + r->off, h.data, dld_bytes * (size_t)h.m,
+                        cudaMemcpyHostToDevice, s->copy_stream);
+      } else {
+        cudaMemcpy2DAsync(s->d_arena + r->off, dld_bytes, h.data, src_ld, row_bytes, (size_t)h.m,
                           cudaMemcpyHostToDevice, s->copy_stream);
-        else
-          cudaMemcpy2DAsync(s->d_arena + r->off, dld_bytes, h.data, (size_t)h.ld * elem,
-                            (size_t)row * elem, (size_t)h.m, cudaMemcpyHostToDevice,
-                            s->copy_stream);
       }
     }
+    flush();
     cudaEvent_t e = take_event(s);
     if (e) cudaEventRecord(e, s->copy_stream);
     for (size_t k = 0; k < newly.size(); ++k) {
@@ -370,6 +431,15 @@ ms_status ms_server_submit(ms_server* s, const ms_matrix* host, double t_arrival
   Request* r = new (std::nothrow) Request();
   if (!r) return MS_ERR_OOM;
   r->host = *host;
+  if (host->m > 0 && host->n > 0) {
+    // pinned host memory that the device maps is copied by the gather kernel
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, host->data) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer != nullptr && pa.device == s->device)
+      r->host_dev = pa.devicePointer;
+    else
+      cudaGetLastError();
+  }
   r->bytes = std::max<size_t>(input_bytes(*host), 256);
   if (r->bytes > s->arena->size()) {
     delete r;
