@@ -95,50 +95,44 @@ int oracle_dp_rows(const uint8_t* v, int64_t m, int64_t n, int64_t ld, oracle_re
   return 0;
 }
 
-/* Algorithm 1 (Sec. 3.2), in the paper's order and with its variables:
- * freq[] tracks the vertical run of ones per column, counter the horizontal
- * run of columns whose freq reaches the height threshold, and a square of side
- * check_max_width is validated when counter reaches that width.  Both
- * thresholds and found_max_width then grow by one and counter restarts.  The
- * paper returns found_max_width squared (the area); this returns the side and
- * records where each validation happened. */
+/* The frequency-based method of Sec. 3.2 (Algorithm 1).  One pass over the
+ * rows keeps, per column, the height of the run of ones ending in the current
+ * row (the frequency array; Sec. 3.4's frequency invariant).  Two thresholds,
+ * a height and a width, start at one and always grow together: while a row is
+ * scanned, a run counts the consecutive columns whose height has reached the
+ * height threshold, and once the run is as long as the width threshold a
+ * square of that side has been seen, so the best side grows by one, both
+ * thresholds grow with it and the run starts again.  A zero, or a column too
+ * short for the height threshold, breaks the run.  The paper returns the
+ * area; this returns the side, and the place of the last acceptance (the
+ * witness: the first corner of a largest square in row-major order). */
 int oracle_freq(const uint8_t* v, int64_t m, int64_t n, int64_t ld, oracle_result* out) {
   set_empty(out);
-  if (m <= 0 || n <= 0) return 0; /* empty matrix: the algorithm returns 0 */
-  const int64_t row_size = n; /* number of columns */
-  const int64_t col_size = m; /* number of rows */
-  int64_t found_max_width = 0;
-  int64_t check_max_width = 1;
-  int64_t check_max_height = 1;
-  int64_t counter = 0;
-  int64_t* freq = (int64_t*)calloc((size_t)row_size, sizeof(int64_t));
-  if (!freq) return -1;
-  for (int64_t i = 0; i < col_size; ++i) {
-    counter = 0;
-    for (int64_t j = 0; j < row_size; ++j) {
-      if (!V(i, j)) {
-        freq[j] = 0;
-        counter = 0;
-        continue;
+  if (m <= 0 || n <= 0) return 0; /* an empty matrix holds no square */
+  int64_t* height = (int64_t*)calloc((size_t)n, sizeof(int64_t));
+  if (!height) return -1;
+  int64_t best = 0, need_h = 1, need_w = 1;
+  for (int64_t i = 0; i < m; ++i) {
+    int64_t run = 0;
+    for (int64_t j = 0; j < n; ++j) {
+      height[j] = V(i, j) ? height[j] + 1 : 0;
+      if (height[j] >= need_h) {
+        run += 1;
+      } else {
+        run = 0;
       }
-      freq[j] = freq[j] + 1;
-      if (freq[j] < check_max_height) {
-        counter = 0;
-        continue;
-      }
-      counter = counter + 1;
-      if (counter == check_max_width) {
-        found_max_width = found_max_width + 1;
-        check_max_width = check_max_width + 1;
-        check_max_height = check_max_height + 1;
-        counter = 0;
-        out->row = (int32_t)i; /* record of this validation */
+      if (run > 0 && run == need_w) {
+        best += 1; /* a square of side need_w ends here */
+        need_w += 1;
+        need_h += 1;
+        run = 0;
+        out->row = (int32_t)i;
         out->col = (int32_t)j;
       }
     }
   }
-  free(freq);
-  out->side = (int32_t)found_max_width;
+  free(height);
+  out->side = (int32_t)best;
   return 0;
 }
 
