@@ -475,15 +475,16 @@ cudaError_t launch_one_fmt(ms_ctx* ctx, const Job& j, cudaStream_t s) {
     const int wpb = (int)std::min<int64_t>(ms::bt::kWarps, (ntiles + ctx->sms - 1) / ctx->sms);
     const unsigned grid = (unsigned)((ntiles + wpb - 1) / wpb);
     const size_t sm = (size_t)wpb * ms::bt::kWarpBytes;
-    if (fuse) {
-      if (allow_smem((const void*)ms::k_bitiles_one<FMT, true>, sm) != cudaSuccess)
-        return cudaGetLastError();
-      ms::k_bitiles_one<FMT, true><<<grid, 32 * wpb, sm, s>>>(j, ntiles, clear);
-    } else {
-      if (allow_smem((const void*)ms::k_bitiles_one<FMT, false>, sm) != cudaSuccess)
-        return cudaGetLastError();
-      ms::k_bitiles_one<FMT, false><<<grid, 32 * wpb, sm, s>>>(j, ntiles, clear);
-    }
+    // aligned byte rows that end in a partial 16-byte chunk take the variant
+    // whose copies read a partial chunk asynchronously
+    const bool ragged = FMT == MS_U8 && j.aligned && j.n % 16 != 0;
+    void (*kern)(const ms::Job, int64_t, ms::TeamSync*) =
+        fuse ? (ragged ? ms::k_bitiles_one<FMT, true, FMT == MS_U8>
+                       : ms::k_bitiles_one<FMT, true, false>)
+             : (ragged ? ms::k_bitiles_one<FMT, false, FMT == MS_U8>
+                       : ms::k_bitiles_one<FMT, false, false>);
+    if (allow_smem((const void*)kern, sm) != cudaSuccess) return cudaGetLastError();
+    kern<<<grid, 32 * wpb, sm, s>>>(j, ntiles, clear);
   } else if (ntiles > 0) {
     ProfScope ps(ctx, s, kProfTile);
     const int64_t warps = (ntiles + 1) / 2;
@@ -838,11 +839,11 @@ ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes) {
     const size_t sm = (size_t)ms::bt::kWarps * ms::bt::kWarpBytes;
     int b0 = 0, b1 = 0;
     // (the variants without the fused fix-up: the launches that fill the GPU)
-    if (allow_smem((const void*)ms::k_bitiles_one<MS_U8, false>, sm) != cudaSuccess ||
-        allow_smem((const void*)ms::k_bitiles_one<MS_BITS32, false>, sm) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, ms::k_bitiles_one<MS_U8, false>,
+    if (allow_smem((const void*)ms::k_bitiles_one<MS_U8, false, false>, sm) != cudaSuccess ||
+        allow_smem((const void*)ms::k_bitiles_one<MS_BITS32, false, false>, sm) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, ms::k_bitiles_one<MS_U8, false, false>,
                                                       32 * ms::bt::kWarps, sm) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, ms::k_bitiles_one<MS_BITS32, false>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, ms::k_bitiles_one<MS_BITS32, false, false>,
                                                       32 * ms::bt::kWarps, sm) != cudaSuccess) {
       cudaGetLastError();
       b0 = b1 = 1;

@@ -62,9 +62,9 @@ struct InGeom {
   static_assert((kDepth & (kDepth - 1)) == 0 && kDepth >= 4, "input ring depth");
 };
 
-// A ragged or unaligned chunk: its first `nvalid` bytes by byte loads, zeros
-// after them (out of line: only edge lanes take it, and the row loop stays
-// small for the instruction cache).
+// A chunk of an unaligned matrix: its first `nvalid` bytes by byte loads,
+// zeros after them (out of line: only such lanes take it, and the row loop
+// stays small for the instruction cache).
 static __device__ __noinline__ void fill_chunk(uint32_t d, const uint8_t* p, int nvalid) {
   uint32_t w[4] = {0u, 0u, 0u, 0u};
   for (int b = 0; b < nvalid; ++b) w[b >> 2] |= (uint32_t)__ldg(p + b) << (8 * (b & 3));
@@ -73,18 +73,23 @@ static __device__ __noinline__ void fill_chunk(uint32_t d, const uint8_t* p, int
 
 // Streams the tile's window rows into the warp's ring.  Bytes: lane l copies
 // chunks l and 32 + l, so that each of the warp's two 16-byte copies reads
-// 512 contiguous bytes and writes them contiguously (cp.async for whole
-// chunks of 16-byte-aligned rows, byte loads with zero fill at a ragged or
-// unaligned edge, nothing beyond the matrix's last column).  Packed: lane l
-// copies word l.
-template <int FMT>
+// 512 contiguous bytes and writes them contiguously (cp.async for chunks of
+// 16-byte-aligned rows, a ragged last chunk with a partial source size that
+// zero-fills the rest; byte loads for unaligned rows; nothing beyond the
+// matrix's last column is read).  Packed: lane l copies word l.
+template <int FMT, bool RAGGED>
 struct Reader {
   using G = InGeom<FMT>;
   const uint8_t* ptr;   // the lane's first chunk (bytes) or word (packed) of window row `row`
   const uint8_t* safe;
   int64_t stride;
   int row, nrows;
-  int mode[2], nvalid[2];  // per chunk: 0 none, 1 async, 2 byte loads
+  // per chunk: 0 no cells; 1..16 an async copy reading that many bytes (the
+  // rest of the 16 zero-filled); 32 + v byte loads of v bytes (unaligned
+  // rows).  Without RAGGED every async copy reads 16 bytes (a ragged chunk
+  // takes the byte loads), which keeps the copy's size a constant: the
+  // variant for matrices whose rows hold whole chunks.
+  int mode[2], nvalid[2];
   uint32_t dst;            // the lane's first chunk in slot 0
 
   __device__ __forceinline__ void init(const Tile& g, int lane, uint32_t ring) {
@@ -98,8 +103,13 @@ struct Reader {
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int64_t valid = g.n - (g.wc0 + 16 * (lane + 32 * k));
-        nvalid[k] = (int)(valid < 16 ? (valid < 0 ? 0 : valid) : 16);
-        mode[k] = nvalid[k] == 0 ? 0 : ((nvalid[k] == 16 && g.aligned) ? 1 : 2);
+        const int v = (int)(valid < 16 ? (valid < 0 ? 0 : valid) : 16);
+        if constexpr (RAGGED) {
+          mode[k] = v == 0 ? 0 : g.aligned ? v : 32 + v;
+        } else {
+          nvalid[k] = v;
+          mode[k] = v == 0 ? 0 : (v == 16 && g.aligned) ? 1 : 2;
+        }
       }
     } else {
       const int64_t col = g.wc0 + 32 * (int64_t)lane;
@@ -130,11 +140,17 @@ struct Reader {
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const uint8_t* p = ptr + 512 * k;
-        if (mode[k] == 1) cp_async(d + 512 * k, ok ? p : safe, 16, ok ? 16 : 0);
-        else if (mode[k] == 2) fill_chunk(d + 512 * k, p, ok ? nvalid[k] : 0);
+        if constexpr (RAGGED) {
+          const int md = mode[k];
+          if (md & 32) fill_chunk(d + 512 * k, p, ok ? md - 32 : 0);
+          else if (md) cp_async(d + 512 * k, ok ? p : safe, 16, ok ? md : 0);
+        } else {
+          if (mode[k] == 1) cp_async(d + 512 * k, ok ? p : safe, 16, ok ? 16 : 0);
+          else if (mode[k] == 2) fill_chunk(d + 512 * k, p, ok ? nvalid[k] : 0);
+        }
       }
     } else {
-      if (mode[0] == 1) cp_async(d, ok ? ptr : safe, 4, ok ? 4 : 0);
+      if (mode[0]) cp_async(d, ok ? ptr : safe, 4, ok ? 4 : 0);
     }
     ptr += stride;
     ++row;
@@ -211,14 +227,14 @@ struct TileOut {
 // `redo` reports that some byte was not, and the tile must run again.
 // plane33 (or null): where the rows of S_33 go from the tile's first S_33
 // row on (row stride pw words).
-template <int FMT, bool B01>
+template <int FMT, bool B01, bool RAGGED>
 __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uint32_t ring,
                                             uint32_t* plane33, int64_t pw) {
   using G = InGeom<FMT>;
   const int lane = threadIdx.x & 31;
   // rows above the window are zeros: clear the level rings
   for (int k = lane; k < kRingWords; k += 32) sts(ring + 4u * k, 0u);
-  Reader<FMT> rd;
+  Reader<FMT, RAGGED> rd;
   rd.init(g, lane, in_ring);
 #pragma unroll
   for (int d = 0; d < G::kDepth; ++d) {
@@ -377,8 +393,9 @@ __device__ __forceinline__ TileOut run_tile(const Tile& g, uint32_t in_ring, uin
 }
 
 // One tile (number t of job j) by the calling warp, in its 8 KB of the
-// block's dynamic shared memory; publishes the tile's key and box.
-template <int FMT>
+// block's dynamic shared memory; publishes the tile's key and box.  RAGGED
+// false: only for matrices whose aligned rows end on a whole 16-byte chunk.
+template <int FMT, bool RAGGED = true>
 __device__ __forceinline__ void tile_one(const Job& j, int64_t t) {
   extern __shared__ __align__(16) unsigned char ms_dyn_smem[];
   const uint32_t base = (uint32_t)__cvta_generic_to_shared(ms_dyn_smem) +
@@ -389,10 +406,10 @@ __device__ __forceinline__ void tile_one(const Job& j, int64_t t) {
   uint32_t* plane33 = j.first33 ? j.bits_scratch + 2 * j.m * (pw + 2) : nullptr;
   TileOut o;
   if constexpr (FMT == MS_U8) {
-    o = run_tile<FMT, true>(g, in_ring, ring, plane33, pw);
-    if (o.redo) o = run_tile<FMT, false>(g, in_ring, ring, plane33, pw);
+    o = run_tile<FMT, true, RAGGED>(g, in_ring, ring, plane33, pw);
+    if (o.redo) o = run_tile<FMT, false, RAGGED>(g, in_ring, ring, plane33, pw);
   } else {
-    o = run_tile<FMT, false>(g, in_ring, ring, plane33, pw);
+    o = run_tile<FMT, false, false>(g, in_ring, ring, plane33, pw);
   }
   if ((threadIdx.x & 31) == 0) {
     if (j.first33) j.first33[t] = o.r1 >= 0 ? o.r0 : 0x7fffffff;
@@ -412,14 +429,16 @@ __device__ __forceinline__ void tile_one(const Job& j, int64_t t) {
 // 32); FUSE: the last block also runs the bitplane fix-up of the box and
 // writes the result, from its own shared memory when the box fits (small
 // matrices; the large ones take the variant without that code, whose tile
-// loop then keeps every register to itself).
-template <int FMT, bool FUSE>
+// loop then keeps every register to itself).  RAGGED: the rows of an aligned
+// byte matrix end in a partial 16-byte chunk (copied asynchronously with a
+// partial source size); without it the copies' size is a constant.
+template <int FMT, bool FUSE, bool RAGGED>
 __global__ void __launch_bounds__(256, 3) k_bitiles_one(const Job job, int64_t ntiles,
                                                          TeamSync* team) {
   grid_dependents_may_launch();
   clear_team(team);
   const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (w < ntiles) bt::tile_one<FMT>(job, w);
+  if (w < ntiles) bt::tile_one<FMT, RAGGED>(job, w);
   if constexpr (FUSE) {
     __shared__ int s_last;
     __syncthreads();

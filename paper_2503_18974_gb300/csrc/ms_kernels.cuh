@@ -88,9 +88,10 @@ __device__ __forceinline__ Tile empty_tile() {
 // holds one row step of both tiles: [tile][lane][kLane bytes].  Lane l copies
 // its own column chunk of window row (s - l + depth) into the slot it
 // consumes at step s with cp.async (no registers held while the copy is in
-// flight), so loads run `depth` steps ahead of use.  Edge and unaligned
-// chunks, and chunks of fewer than 4 bytes, are loaded synchronously into the
-// same slot.  32-byte chunks (uint8, P = 32) get half as many, twice as large
+// flight), so loads run `depth` steps ahead of use; a ragged last chunk is
+// copied with a partial source size, the rest of its slot zero-filled.
+// Chunks of unaligned rows, and chunks of fewer than 4 bytes at the edge, are
+// loaded synchronously into the same slot.  32-byte chunks (uint8, P = 32) get half as many, twice as large
 // slots.
 constexpr int kRingWarpBytes = 8192;
 
@@ -148,8 +149,10 @@ struct AsyncReader {
   const uint8_t* safe;  // a valid address (zero-fill copies read nothing)
   int64_t stride;
   int row, nrows;
-  int mode;             // 0: no cells (slots stay zero), 1: async copy, 2: synchronous
-  int nvalid;
+  // 0: no cells (slots stay zero); 1..kBytes: an async copy reading that many
+  // bytes of the chunk (the rest zero-filled); 64 + v: v bytes by synchronous
+  // byte loads
+  int mode;
   uint32_t dst;         // this lane's place in slot 0
   uint32_t lshift;      // chunks under 4 bytes: bit offset of the chunk in its copied word
 
@@ -164,10 +167,12 @@ struct AsyncReader {
     if constexpr (FMT == MS_U8) {
       stride = g.ld;
       const int64_t valid = g.n - col;
-      nvalid = (int)(valid < P ? (valid < 0 ? 0 : valid) : P);
+      const int nvalid = (int)(valid < P ? (valid < 0 ? 0 : valid) : P);
       if constexpr (P >= 4) {
+        // (a ragged last chunk of an aligned matrix is copied asynchronously
+        // too: the copy reads its valid bytes and zero-fills the rest)
         ptr = g.base + (g.wr0 + first_row) * g.ld + col;
-        mode = nvalid == 0 ? 0 : ((nvalid == P && g.aligned) ? 1 : 2);
+        mode = nvalid == 0 ? 0 : g.aligned ? nvalid : 64 + nvalid;
       } else {
         // 1- and 2-byte chunks are fetched as the aligned 4-byte word holding
         // them (asynchronously, like the wider chunks), unless that word
@@ -176,13 +181,12 @@ struct AsyncReader {
         const bool word_ok = g.aligned && col4 + 4 <= g.n;
         ptr = g.base + (g.wr0 + first_row) * g.ld + (word_ok ? col4 : col);
         lshift = word_ok ? (uint32_t)(8 * (col - col4)) : 0u;
-        mode = nvalid == 0 ? 0 : ((nvalid == P && word_ok) ? 1 : 2);
+        mode = nvalid == 0 ? 0 : (nvalid == P && word_ok) ? 4 : 64 + nvalid;
       }
     } else {
       stride = g.ld * 4;
       ptr = g.base + ((g.wr0 + first_row) * g.ld + (col >> 5)) * 4;
-      nvalid = 4;
-      mode = col < g.n ? 1 : 0;
+      mode = col < g.n ? 4 : 0;
     }
     // slots start as zeros: mode 0 never writes, the others overwrite
     uint32_t zero[G::kLane / 4];
@@ -196,24 +200,26 @@ struct AsyncReader {
   __device__ __forceinline__ void issue(int slot) {
     const bool ok = (unsigned)row < (unsigned)nrows;
     const uint32_t d = dst + slot * G::kSlot;
-    if (mode == 1) {
-      const uint8_t* src = ok ? ptr : safe;
-      if constexpr (kBytes > 16) {
-        cp_async(d, src, 16, ok ? 16 : 0);
-        cp_async(d + 16, src + 16, 16, ok ? 16 : 0);
-      } else if constexpr (kBytes < 4) {
-        cp_async(d, src, 4, ok ? 4 : 0);
-      } else {
-        cp_async(d, src, kBytes, ok ? kBytes : 0);
-      }
-    } else if (mode == 2) {
+    const int md = mode;
+    if (md & 64) {
       constexpr int NW = G::kLane / 4;
       uint32_t w[NW];
 #pragma unroll
       for (int b = 0; b < NW; ++b) w[b] = 0u;
       if (ok)
-        for (int b = 0; b < nvalid; ++b) w[b >> 2] |= (uint32_t)__ldg(ptr + b) << (8 * (b & 3));
+        for (int b = 0; b < md - 64; ++b) w[b >> 2] |= (uint32_t)__ldg(ptr + b) << (8 * (b & 3));
       st_shared_chunk<G::kLane>(d, w);
+    } else if (md) {
+      const uint8_t* src = ok ? ptr : safe;
+      if constexpr (kBytes > 16) {
+        const int v0 = ok ? min(md, 16) : 0, v1 = ok ? max(md - 16, 0) : 0;
+        cp_async(d, src, 16, v0);
+        cp_async(d + 16, v1 ? src + 16 : safe, 16, v1);
+      } else if constexpr (kBytes < 4) {
+        cp_async(d, src, 4, ok ? 4 : 0);
+      } else {
+        cp_async(d, src, kBytes, ok ? md : 0);
+      }
     }
     ptr += stride;
     ++row;

@@ -253,6 +253,40 @@ def test_nonzero_bytes_and_strides(ctx):
     assert ctx.max_square(w, n=900).cpu().tolist() == [K, r, c, 0]
 
 
+@pytest.mark.parametrize("tile_kind,lane_cols", [(1, 4), (1, 8), (1, 16), (1, 32), (2, 0)])
+def test_aligned_rows_with_ragged_last_chunk(ctx, tile_kind, lane_cols):
+    """16-byte-aligned rows (a padded row stride) whose width is not a multiple
+    of 16: the last chunk of each row is copied with a partial source size.
+    The padding bytes are ones, and against the right edge sits a block of
+    ones s rows high and s - 3 columns wide: a copy that read past column n
+    would see an s-square there."""
+    ctx.set_tuning(band_rows=64, lane_cols=lane_cols, tile_kind=tile_kind)
+    try:
+        views, exps = [], []
+        for t, n in enumerate([17, 100, 527, 1031, 2047, 3003]):
+            m = 230
+            a = gen.bernoulli_u8(m, n, 0.8, seed=9100 + t)
+            s = min(60, n)
+            a[40:40 + s, n - max(s - 3, 1):n] = 1
+            ld = (n + 15) // 16 * 16 + 16
+            big = torch.ones((m, ld), dtype=torch.uint8, device=DEV)
+            big[:, :n] = to_dev(a)
+            x = big[:, :n]
+            (K, r, c), dref = oracle.dp(a)
+            exp = [K, r, c, 0]
+            assert ctx.max_square(x).cpu().tolist() == exp, (n, tile_kind, lane_cols)
+            dp, res = ctx.dp_map(x)
+            assert res.cpu().tolist() == exp, (n, "map")
+            assert np.array_equal(dp.cpu().numpy(), dref), (n, "map values")
+            views.append(x)
+            exps.append(exp)
+        for kind in (0, 1, 2):
+            ctx.set_tuning(band_rows=64, tile_kind=kind)
+            assert ctx.batch(views).cpu().tolist() == exps, ("batch", kind)
+    finally:
+        ctx.set_tuning()
+
+
 def test_dp_map_store_alignments(ctx):
     """The dp map through each store path: 32-byte rows (256-bit stores),
     16-byte rows (128-bit stores) and unaligned rows (scalar stores), with
