@@ -23,6 +23,7 @@ struct ms_ctx {
   int device = 0;
   int sms = 1;        // streaming multiprocessors of the device
   int bit_slots = 0;  // bitplane tile warps resident at once on the device
+  size_t small_smem[4] = {0, 0, 0, 0};  // dynamic shared memory of a small-matrix block, by class
   size_t budget = 0;  // 0 = unlimited
   size_t held = 0;    // bytes of device workspace currently held
   ms_tuning tuning{};
@@ -354,7 +355,7 @@ struct SmallClass {
 };
 constexpr SmallClass kSmall[4] = {{2048, 128, 8},    // 16 KB
                                   {6144, 256, 4},    // 48 KB
-                                  {14336, 512, 2},   // 112 KB
+                                  {14320, 512, 2},   // 112 KB (two blocks fit 228 KB)
                                   {28672, 1024, 1}};  // 224 KB
 constexpr int kFixClusterBlocks = 8;  // a single large matrix's fix-up cluster (portable size)
 
@@ -834,6 +835,31 @@ ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes) {
   }
   ctx->sms = std::max(ctx->sms, 1);
   {
+    // small-matrix blocks: each class's share of an SM's shared memory (its
+    // blocks per SM at once), two planes of its largest matrix at least; what
+    // lies beyond the planes stages input rows
+    int sm_sm = 0, optin = 0, reserved = 0;
+    cudaFuncAttributes fa{};
+    const bool ok = cudaDeviceGetAttribute(&sm_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                           device) == cudaSuccess &&
+                    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                           device) == cudaSuccess &&
+                    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock,
+                                           device) == cudaSuccess &&
+                    cudaFuncGetAttributes(&fa, ms::k_batch_small) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    for (int c = 0; c < 4; ++c) {
+      const size_t planes = 2 * (size_t)kSmall[c].words * 4;
+      size_t share = 0;
+      if (ok) {
+        const size_t st = fa.sharedSizeBytes, per = (size_t)sm_sm / kSmall[c].per_sm;
+        share = per > (size_t)reserved + st ? per - (size_t)reserved - st : 0;
+        share = std::min(share, (size_t)optin > st ? (size_t)optin - st : 0) & ~(size_t)15;
+      }
+      ctx->small_smem[c] = std::max(planes, share);
+    }
+  }
+  {
     // bitplane tiles: blocks of kWarps warps that fit an SM at once (both
     // input formats; the smaller count)
     const size_t sm = (size_t)ms::bt::kWarps * ms::bt::kWarpBytes;
@@ -1271,7 +1297,7 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
     for (int c = 3; c >= 0; --c) {
       const int n = (int)small[c].size();
       if (n == 0) continue;
-      const size_t sm = 2 * (size_t)kSmall[c].words * 4;
+      const size_t sm = ctx->small_smem[c];
       if (allow_smem((const void*)ms::k_batch_small, sm) != cudaSuccess) return MS_ERR_CUDA;
       const int grid = std::min(n, kSmall[c].per_sm * ctx->sms);
       ms::k_batch_small<<<grid, kSmall[c].threads, sm, ss>>>(d_jobs, d_order + off[c], n,
