@@ -39,10 +39,11 @@ struct ms_ctx {
   int64_t first33_cap = 0;
   int64_t bitfix_cap = 0;        // uint32 words
   ms::TeamSync* d_sync1 = nullptr;  // barrier of a single matrix's fix-up team
-  // a second stream for the small matrices of a batch, forked from and
-  // joined back into the caller's stream with two events
-  cudaStream_t side = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // streams for the small matrices of a batch, one per size class, forked
+  // from and joined back into the caller's stream with events
+  static constexpr int kSides = 4;
+  cudaStream_t side[kSides] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kSides] = {};
 
   // batch job table: device copy, the host image it was uploaded from, and a
   // pinned staging buffer guarded by an event
@@ -882,9 +883,11 @@ ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes) {
     delete ctx;
     return MS_ERR_OOM;
   }
-  if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+  bool made = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < ms_ctx::kSides && made; ++k)
+    made = cudaStreamCreateWithFlags(&ctx->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ctx->ev_join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!made) {
     cudaGetLastError();
     ms_destroy(ctx);
     return MS_ERR_CUDA;
@@ -915,9 +918,11 @@ ms_status ms_destroy(ms_ctx* ctx) {
     if (ctx->h_stage) cudaFreeHost(ctx->h_stage);
     if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
     if (ctx->d_sync1) cudaFree(ctx->d_sync1);
-    if (ctx->side) cudaStreamDestroy(ctx->side);
+    for (int k = 0; k < ms_ctx::kSides; ++k) {
+      if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+      if (ctx->ev_join[k]) cudaEventDestroy(ctx->ev_join[k]);
+    }
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     for (auto& ps : ctx->prof_pool) {
       cudaEventDestroy(ps.a);
       cudaEventDestroy(ps.b);
@@ -1224,31 +1229,38 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   ms::TeamSync* d_syncs = reinterpret_cast<ms::TeamSync*>(d_clear + 32);
   if (cudaMemsetAsync(d_clear, 0, clear_bytes, s) != cudaSuccess) return MS_ERR_CUDA;
 
-  // The small matrices run on the context's second stream, forked from the
-  // caller's after the clear and joined back at the end, so that they share
-  // the GPU with the large matrices' tiles and fix-up (while kernels are
-  // timed by ms_profile_*, everything stays on the caller's stream).
-  const bool fork = nsmall > 0 && (nbit > 0 || ntasks > 0) && !ctx->prof_on;
-  cudaStream_t ss = s;
-  // joins the second stream back on every way out once it is forked (a
+  // The small matrices run on the context's side streams (one per size
+  // class), forked from the caller's after the clear and joined back at the
+  // end, so that the classes and the large matrices' tiles and fix-up share
+  // the GPU and fill each other's tails (while kernels are timed by
+  // ms_profile_*, everything stays on the caller's stream).
+  const bool fork = nsmall > 0 && !ctx->prof_on;
+  cudaStream_t ss[4] = {s, s, s, s};
+  // joins the side streams back on every way out once they are forked (a
   // capture must not end with a branch left open)
   struct Join {
     ms_ctx* c;
     cudaStream_t s;
     bool on = false;
+    bool join() {
+      bool ok = true;
+      for (int k = 0; k < ms_ctx::kSides; ++k)
+        ok = cudaEventRecord(c->ev_join[k], c->side[k]) == cudaSuccess &&
+             cudaStreamWaitEvent(s, c->ev_join[k], 0) == cudaSuccess && ok;
+      on = false;
+      return ok;
+    }
     ~Join() {
-      if (on) {
-        cudaEventRecord(c->ev_join, c->side);
-        cudaStreamWaitEvent(s, c->ev_join, 0);
-      }
+      if (on) join();
     }
   } join{ctx, s};
   if (fork) {
-    if (cudaEventRecord(ctx->ev_fork, s) != cudaSuccess ||
-        cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0) != cudaSuccess)
-      return MS_ERR_CUDA;
+    if (cudaEventRecord(ctx->ev_fork, s) != cudaSuccess) return MS_ERR_CUDA;
     join.on = true;
-    ss = ctx->side;
+    for (int k = 0; k < ms_ctx::kSides; ++k) {
+      if (cudaStreamWaitEvent(ctx->side[k], ctx->ev_fork, 0) != cudaSuccess) return MS_ERR_CUDA;
+      ss[k] = ctx->side[k];
+    }
   }
   {
     ProfScope ps(ctx, s, kProfTile);
@@ -1300,7 +1312,7 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
       const size_t sm = ctx->small_smem[c];
       if (allow_smem((const void*)ms::k_batch_small, sm) != cudaSuccess) return MS_ERR_CUDA;
       const int grid = std::min(n, kSmall[c].per_sm * ctx->sms);
-      ms::k_batch_small<<<grid, kSmall[c].threads, sm, ss>>>(d_jobs, d_order + off[c], n,
+      ms::k_batch_small<<<grid, kSmall[c].threads, sm, ss[c]>>>(d_jobs, d_order + off[c], n,
                                                              d_queues + 3 + c);
       if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
     }
@@ -1319,12 +1331,7 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
       k_fixup_mixed<<<count, ms::kFixWarps * 32, smf, s>>>(d_jobs, count);
     }
   }
-  if (join.on) {
-    join.on = false;
-    if (cudaEventRecord(ctx->ev_join, ctx->side) != cudaSuccess ||
-        cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess)
-      return MS_ERR_CUDA;
-  }
+  if (join.on && !join.join()) return MS_ERR_CUDA;
   return cuda_status(cudaGetLastError());
 }
 

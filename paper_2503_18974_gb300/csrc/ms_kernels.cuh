@@ -969,6 +969,53 @@ __device__ __forceinline__ void grow_pass(const Plane& L, Plane& O, int o_r1, in
   O.aw1 = box[3];
 }
 
+// Multi-way test by the team, no plane written: how many of the T (<= 7)
+// sides t_k = a + d[k] (ascending, 0 < d[k] <= a) have a corner, from L =
+// S_a over its active box clipped to rows [o_r0, o_r1) x words [o_w0, o_w1).
+// A corner of a t-square is a corner of every smaller square, so the sides
+// with a corner are a prefix: a word tests the sides above its best so far,
+// the largest first, and stops at its first hit.
+constexpr int kTeamWays = 7;
+__device__ __forceinline__ int probe_pass(const Plane& L, int o_r0, int o_w0, int o_r1, int o_w1,
+                                          const int (&d)[kTeamWays], int T, int64_t n,
+                                          PassBox& pb) {
+  const int r0 = max(L.ar0, o_r0), r1 = min(L.ar1, o_r1);
+  const int w0 = max(L.aw0, o_w0), w1 = min(L.aw1, o_w1);
+  const int wlast = (int)((n - 1) >> 5);
+  const uint32_t lastmask = (n & 31) ? ((1u << (n & 31)) - 1u) : 0xffffffffu;
+  int found = 0;
+  pb.begin();
+  for_cells(*pb.tm, r1 - r0, w1 - w0, [&](int rr, int cc) {
+    const int i = r0 + rr, w = w0 + cc;
+    const uint32_t* row = L.p + (i - L.r0) * L.pitch - L.w0;
+    const uint32_t a0 = row[w] & (w == wlast ? lastmask : 0xffffffffu);
+    if (!a0) return;
+#pragma unroll
+    for (int k = kTeamWays - 1; k >= 0; --k) {
+      if (k >= T) continue;
+      if (k < found) break;
+      const int dk = d[k], q = dk >> 5, r = dk & 31;
+      if (i - dk < L.ar0) continue;  // the square's top row lies above every set bit
+      const uint32_t* up = row - dk * L.pitch;
+      const int wq = w - q;
+      const bool q_ok = wq >= L.aw0, q1_ok = wq - 1 >= L.aw0;
+      uint32_t a2 = q_ok ? row[wq] : 0u;
+      uint32_t a3 = q_ok ? up[wq] : 0u;
+      if (r) {
+        a2 = (a2 << r) | ((q1_ok ? row[wq - 1] : 0u) >> (32 - r));
+        a3 = (a3 << r) | ((q1_ok ? up[wq - 1] : 0u) >> (32 - r));
+      }
+      if (a0 & up[w] & a2 & a3) {
+        found = k + 1;
+        break;
+      }
+    }
+  });
+  int box[4];
+  pb.end(0x7fffffff, found - 1, 0x7fffffff, -1, box);
+  return box[1];  // the team's largest count
+}
+
 // Geometry of the bitplane fix-up of box [rlo, rhi) x [clo, chi): S_32 is
 // built on rows [ra, rhi) x words [wa, whi) (the box grown by 32 up and
 // left) from input rows [pa, rhi) x words [wa-1, whi).
@@ -1141,10 +1188,19 @@ struct Runs {
   }
   template <class F>
   __device__ __forceinline__ void each(F&& f) const {
-    const int units = rows * nseg;
-    for (int u = threadIdx.x; u < units; u += blockDim.x) {
-      const int r = u / nseg, c0 = (u - r * nseg) * len;
+    if (nseg == 0) return;
+    // unit u = r * nseg + seg, stepped by blockDim without a division per unit
+    const int bd = (int)blockDim.x, dr = bd / nseg, ds = bd - dr * nseg;
+    int r = (int)threadIdx.x / nseg, seg = (int)threadIdx.x - r * nseg;
+    while (r < rows) {
+      const int c0 = seg * len;
       f(r, c0, min(cols, c0 + len));
+      r += dr;
+      seg += ds;
+      if (seg >= nseg) {
+        seg -= nseg;
+        ++r;
+      }
     }
   }
 };
@@ -1538,10 +1594,17 @@ __device__ __forceinline__ void fixup_bits(const Job& j, int rlo, int rhi, int c
     nxt = Plane{freed, rlo, wlo, BW, 0, 0, 0, 0};
   }
   Plane probe = nxt;  // tests write nothing
+  // search: up to seven sides per pass (fewer team barriers than halving)
   while (hi - lo > 1) {
-    const int t = (lo + hi) / 2;
-    grow_pass(cur, probe, rhi, whi, t - a, j.n, false, nullptr, pb);
-    if (!probe.empty()) lo = t; else hi = t;
+    const int span = hi - lo, T = min(kTeamWays, span - 1);
+    int d[kTeamWays];
+#pragma unroll
+    for (int k = 0; k < kTeamWays; ++k) d[k] = lo + (k + 1) * span / (T + 1) - a;
+    const int ok = probe_pass(cur, probe.r0, probe.w0, rhi, whi, d, T, j.n, pb);
+    const int nlo = ok ? lo + ok * span / (T + 1) : lo;
+    const int nhi = ok < T ? lo + (ok + 1) * span / (T + 1) : hi;
+    lo = nlo;
+    hi = nhi;
   }
   // 5. witness: the first set bit of S_lo inside the box (and, for the
   //    all-largest-squares call, every set bit: all of them lie in the box)
