@@ -19,11 +19,14 @@
 using ms::Job;
 using ms::JobState;
 
+// size classes of the batch's small matrices (solved whole, one block each)
+constexpr int kClasses = 5;
+
 struct ms_ctx {
   int device = 0;
   int sms = 1;        // streaming multiprocessors of the device
   int bit_slots = 0;  // bitplane tile warps resident at once on the device
-  size_t small_smem[4] = {0, 0, 0, 0};  // dynamic shared memory of a small-matrix block, by class
+  size_t small_smem[kClasses] = {};  // dynamic shared memory of a small-matrix block, by class
   size_t budget = 0;  // 0 = unlimited
   size_t held = 0;    // bytes of device workspace currently held
   ms_tuning tuning{};
@@ -41,7 +44,7 @@ struct ms_ctx {
   ms::TeamSync* d_sync1 = nullptr;  // barrier of a single matrix's fix-up team
   // streams for the small matrices of a batch, one per size class, forked
   // from and joined back into the caller's stream with events
-  static constexpr int kSides = 4;
+  static constexpr int kSides = kClasses;
   cudaStream_t side[kSides] = {};
   cudaEvent_t ev_fork = nullptr, ev_join[kSides] = {};
 
@@ -354,10 +357,10 @@ struct SmallClass {
   int64_t words;
   int threads, per_sm;
 };
-constexpr SmallClass kSmall[4] = {{2048, 128, 8},    // 16 KB
-                                  {6144, 256, 4},    // 48 KB
-                                  {14320, 512, 2},   // 112 KB (two blocks fit 228 KB)
-                                  {28672, 1024, 1}};  // 224 KB
+constexpr SmallClass kSmall[kClasses] = {{512, 64, 16}, {2048, 128, 8},     // 16 KB
+                                         {6144, 256, 4},     // 48 KB
+                                         {14320, 512, 2},    // 112 KB (two blocks fit 228 KB)
+                                         {28672, 1024, 1}};  // 224 KB
 constexpr int kFixClusterBlocks = 8;  // a single large matrix's fix-up cluster (portable size)
 
 
@@ -849,7 +852,7 @@ ms_status ms_create(ms_ctx** out, int device, size_t workspace_budget_bytes) {
                                            device) == cudaSuccess &&
                     cudaFuncGetAttributes(&fa, ms::k_batch_small) == cudaSuccess;
     if (!ok) cudaGetLastError();
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < kClasses; ++c) {
       const size_t planes = 2 * (size_t)kSmall[c].words * 4;
       size_t share = 0;
       if (ok) {
@@ -1003,14 +1006,14 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   const ms_tuning tune = effective_tuning(ctx, ins_host, count, true);
   const int mode = tune.lane_cols > 0 ? 1 : tune.tile_kind;
   std::vector<Job> jobs((size_t)count);
-  std::vector<int32_t> small[4];  // matrices for the small-matrix launches, by class
+  std::vector<int32_t> small[kClasses];  // matrices for the small-matrix launches, by class
   int64_t carry = 0, progress = 0, work_dp = 0, work_bit = 0;
   for (int32_t i = 0; i < count; ++i) {
     jobs[i] = plan_job(tune, &ins_host[i], false, 16, 0);  // dp recurrence: P <= 16
     Job& j = jobs[i];
     const bool empty = j.m <= 0 || j.n <= 0;
     const int64_t pw = empty ? 0 : ms::small::plane_words(j.m, j.n);
-    if (mode == 0 && pw <= kSmall[3].words) {
+    if (mode == 0 && pw <= kSmall[kClasses - 1].words) {
       j.tile_kind = 2;  // solved whole; no tiles, no fix-up state
       j.strips = j.bands = 0;
       int c = 0;
@@ -1223,8 +1226,9 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   const ms::FixTask* d_fix = reinterpret_cast<const ms::FixTask*>(ctx->d_table + o_fix);
   const int32_t* d_order = reinterpret_cast<const int32_t*>(ctx->d_table + o_order);
   unsigned char* d_clear = ctx->d_table + o_clear;
-  // queue counters: tile pairs, uint8 and packed bitplane tiles, four small
+  // queue counters: tile pairs, uint8 and packed bitplane tiles, the small
   // classes
+  static_assert(3 + kClasses <= 8, "eight queue counters");
   int* d_queues = reinterpret_cast<int*>(d_clear);
   ms::TeamSync* d_syncs = reinterpret_cast<ms::TeamSync*>(d_clear + 32);
   if (cudaMemsetAsync(d_clear, 0, clear_bytes, s) != cudaSuccess) return MS_ERR_CUDA;
@@ -1235,7 +1239,8 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
   // the GPU and fill each other's tails (while kernels are timed by
   // ms_profile_*, everything stays on the caller's stream).
   const bool fork = nsmall > 0 && !ctx->prof_on;
-  cudaStream_t ss[4] = {s, s, s, s};
+  cudaStream_t ss[kClasses];
+  for (int c = 0; c < kClasses; ++c) ss[c] = s;
   // joins the side streams back on every way out once they are forked (a
   // capture must not end with a branch left open)
   struct Join {
@@ -1301,12 +1306,12 @@ ms_status ms_batch(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_res
       if (cudaGetLastError() != cudaSuccess) return MS_ERR_CUDA;
     }
     // small matrices solved whole, the largest class first
-    int off[4], o = 0;
-    for (int c = 0; c < 4; ++c) {
+    int off[kClasses], o = 0;
+    for (int c = 0; c < kClasses; ++c) {
       off[c] = o;
       o += (int)small[c].size();
     }
-    for (int c = 3; c >= 0; --c) {
+    for (int c = kClasses - 1; c >= 0; --c) {
       const int n = (int)small[c].size();
       if (n == 0) continue;
       const size_t sm = ctx->small_smem[c];
