@@ -289,8 +289,13 @@ ms_status ms_get_tuning(ms_ctx* ctx, ms_tuning* t);
  * matrices for each candidate tuning -- band heights 32..1024 and the
  * automatic choice, lane widths 2..32 and the automatic choice (single
  * matrices only), and for
- * MS_BITS32 size-only work both packed paths --
- * keeps the fastest, and caches it in the context under the workload's class
+ * MS_BITS32 size-only work both packed paths, and for batches the three
+ * tile kinds -- in three interleaved rounds, each candidate keeping its
+ * fastest; batches are timed as replays of a CUDA graph of the call on a
+ * private stream (ordered after the caller's work), so that the host's
+ * planning of a call does not weigh in.  A candidate must beat the best
+ * earlier one by 2% to replace it (near-ties keep the automatic choice, which
+ * comes first).  Keeps the chosen one and caches it in the context under the workload's class
  * (entry point, format mix, log2 of the cell count, log2 of the matrix
  * count).  Later calls of that class with ms_tuning.band_rows == 0 and
  * lane_cols == 0 use the cached choice.  `outs_dev` receives results (count entries) and is

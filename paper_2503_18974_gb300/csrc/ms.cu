@@ -1376,34 +1376,83 @@ ms_status ms_autotune(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_
   const ms_tuning saved = ctx->tuning;
   const auto saved_cache = ctx->tuned;
   ctx->tuned.clear();
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MS_ERR_CUDA;
-  float best_ms = 1e30f;
-  ms_tuning best = cands[0];
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // Batches are timed as graph replays on a private stream (ordered after
+  // the caller's work): a call's host-side planning, which a caller that
+  // captures or repeats the call does not wait for, must not decide the
+  // choice.  Single matrices are timed as plain calls on the caller's stream.
+  cudaStream_t ts = s;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      (batch && (cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) != cudaSuccess ||
+                 cudaEventRecord(e0, s) != cudaSuccess || cudaStreamWaitEvent(ts, e0, 0) != cudaSuccess))) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ts != s) cudaStreamDestroy(ts);
+    ctx->tuning = saved;
+    ctx->tuned = saved_cache;
+    return MS_ERR_CUDA;
+  }
+  // Every candidate is timed in three interleaved rounds (a slow moment of
+  // the GPU then costs each candidate one round at most) and keeps its
+  // fastest; a later candidate must beat the best so far by 2% to replace
+  // it, so near-ties keep the earlier one (the automatic choice comes first).
+  std::vector<float> best_of(cands.size(), 1e30f);
   ms_status err = MS_OK;
-  for (const ms_tuning& t : cands) {
-    ctx->tuning = t;
-    auto run = [&]() -> ms_status {
-      return batch ? ms_batch(ctx, ins_host, count, outs_dev, stream)
-                   : ms_max_square(ctx, ins_host, outs_dev, stream);
-    };
-    err = run();  // warm-up (also sizes the workspace)
-    if (err != MS_OK) break;
-    const int reps = 5;
-    cudaEventRecord(e0, s);
-    for (int k = 0; k < reps && err == MS_OK; ++k) err = run();
-    cudaEventRecord(e1, s);
-    if (err != MS_OK || cudaEventSynchronize(e1) != cudaSuccess) {
-      if (err == MS_OK) err = MS_ERR_CUDA;
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = t;
+  const int reps = 3;
+  for (int round = 0; round < 3 && err == MS_OK; ++round) {
+    for (size_t c = 0; c < cands.size() && err == MS_OK; ++c) {
+      ctx->tuning = cands[c];
+      auto run = [&]() -> ms_status {
+        return batch ? ms_batch(ctx, ins_host, count, outs_dev, ts)
+                     : ms_max_square(ctx, ins_host, outs_dev, ts);
+      };
+      err = run();  // warm-up (also sizes the workspace and uploads a batch's table)
+      if (err != MS_OK) break;
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      if (batch) {
+        if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+          err = MS_ERR_CUDA;
+          break;
+        }
+        const ms_status ec = run();
+        const cudaError_t ee = cudaStreamEndCapture(ts, &graph);
+        if (ec != MS_OK || ee != cudaSuccess ||
+            cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess ||
+            cudaGraphLaunch(exec, ts) != cudaSuccess) {
+          err = ec != MS_OK ? ec : MS_ERR_CUDA;
+        }
+      }
+      if (err == MS_OK) {
+        cudaEventRecord(e0, ts);
+        for (int k = 0; k < reps && err == MS_OK; ++k)
+          err = batch ? (cudaGraphLaunch(exec, ts) == cudaSuccess ? MS_OK : MS_ERR_CUDA) : run();
+        cudaEventRecord(e1, ts);
+        if (err == MS_OK && cudaEventSynchronize(e1) != cudaSuccess) err = MS_ERR_CUDA;
+      }
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      if (err != MS_OK) {
+        cudaGetLastError();
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best_of[c] = std::min(best_of[c], ms);
     }
   }
+  if (ts != s) {
+    // the caller's stream resumes after the private one
+    cudaEventRecord(e1, ts);
+    cudaStreamWaitEvent(s, e1, 0);
+    cudaStreamSynchronize(ts);
+    cudaStreamDestroy(ts);
+  }
+  size_t pick = 0;
+  for (size_t c = 1; c < cands.size(); ++c)
+    if (best_of[c] < 0.98f * best_of[pick]) pick = c;
+  const ms_tuning best = cands[pick];
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->tuning = saved;

@@ -212,9 +212,10 @@ __device__ __forceinline__ void solve_matrix(const Job& j, uint32_t* smem, int64
 // the queue counter, which starts at zero): each fits two planes in the
 // block's dynamic shared memory.
 //
-// Launched per size class with blocks of 128 to 1024 threads (every variant
-// fits 64 registers a thread, so the SM holds 1024 of its threads: eight
-// small blocks of tiny matrices at once, or one block of the largest).
+// Launched per size class with blocks of 64 to 1024 threads (every variant
+// fits 64 registers a thread, so the SM holds 1024 of its threads: sixteen
+// blocks of the tiniest matrices at once, or one block of the largest).  The
+// part of a block's shared memory beyond the two planes stages input rows.
 static __global__ void __launch_bounds__(1024, 1)
     k_batch_small(const Job* __restrict__ jobs, const int32_t* __restrict__ order, int count,
                   int* queue) {
