@@ -650,8 +650,13 @@ def _measure(args, ms, ctx, name, device, stream, pg, clocks, e2e, steps):
                        "same K steps re-run); step_frac: algorithmic bytes / ms_per_step "
                        "(the whole call)"}
         if kern_ms / steps > ms_step * 1.02:
-            roof["note"] = ("per-launch event pairs between many short launches add gaps; "
-                            "the kernel time here is an upper bound")
+            roof["note"] = (
+                "timed kernels run one after another on the caller's stream (the batch's "
+                "small-matrix classes and large matrices do not overlap as in the graph-"
+                "replayed step), so the kernel time exceeds the step: an upper bound"
+                if batch_headline else
+                "per-launch event pairs between many short launches add gaps; "
+                "the kernel time here is an upper bound")
     launches = int(prof.tile_launches + prof.fixup_launches + prof.other_launches)
 
     compare = None
