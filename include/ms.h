@@ -289,8 +289,9 @@ ms_status ms_get_tuning(ms_ctx* ctx, ms_tuning* t);
  * matrices for each candidate tuning -- band heights 32..1024 and the
  * automatic choice, lane widths 2..32 and the automatic choice (single
  * matrices only), and for
- * MS_BITS32 size-only work both packed paths, and for batches the three
- * tile kinds -- in three interleaved rounds, each candidate keeping its
+ * MS_BITS32 size-only work both packed paths, for batches the three tile
+ * kinds and for single matrices bitplane tiles forced (tile_kind 2) with
+ * each band height -- in three interleaved rounds, each candidate keeping its
  * fastest; batches are timed as replays of a CUDA graph of the call on a
  * private stream (ordered after the caller's work), so that the host's
  * planning of a call does not weigh in.  A candidate must beat the best

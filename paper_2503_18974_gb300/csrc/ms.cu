@@ -1357,15 +1357,17 @@ ms_status ms_autotune(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_
   const int lanes[] = {0, 2, 4, 8, 16, 32};
   // batches also choose how their matrices are tiled: small ones whole and
   // large ones as bitplane tiles (0), everything as dp-recurrence tile pairs
-  // (1) or everything as bitplane tiles (2)
-  for (int tk = 0; tk <= (batch ? 2 : 0); ++tk)
+  // (1) or everything as bitplane tiles (2); a single matrix between the
+  // automatic choice (0) and bitplane tiles with each band height (2)
+  for (int tk = 0; tk <= 2; ++tk)
     for (int pp = 0; pp <= (packed_single ? 1 : 0); ++pp)
       for (int lc : lanes)
         for (int r : rows) {
           // the bitplane search has no band height or lane width; batches use
-          // the automatic lane width (at most 16)
+          // the automatic lane width (at most 16), bitplane tiles have none
           if (pp == 1 && (r != 0 || lc != 0)) continue;
           if (batch && lc != 0) continue;
+          if (!batch && (tk == 1 || (tk == 2 && (lc != 0 || pp != 0)))) continue;
           ms_tuning t{};
           t.band_rows = r;
           t.packed_path = pp;

@@ -353,6 +353,41 @@ def test_batch_mixed_shapes_and_formats(ctx):
     assert outbuf.cpu().tolist() == exps
 
 
+def plane_words(m, n):
+    """Words of one small-matrix plane: rows at an odd pitch, rounded to 4."""
+    w = (n + 31) // 32
+    return (m * (w | 1) + 3) // 4 * 4
+
+
+@pytest.mark.parametrize("limit,w", [(512, 1), (2048, 1), (6144, 3), (14320, 5), (28672, 7)])
+def test_batch_small_class_boundaries(ctx, limit, w):
+    """Matrices whose plane is exactly a size class's limit and one row more
+    (the next class, or bitplane tiles past the largest), 32w columns and
+    32w - 5 (a ragged last chunk), uint8 in aligned rows and packed; random
+    cells with a planted square against the right edge.  Every result equals
+    the oracle's, in one batch and in a batch of one."""
+    m_at = limit // w
+    assert plane_words(m_at, 32 * w) == limit and plane_words(m_at + 1, 32 * w) > limit
+    mats, exps = [], []
+    for k, (m, n) in enumerate([(m_at, 32 * w), (m_at + 1, 32 * w), (m_at, 32 * w - 5),
+                                (m_at + 1, 32 * w - 5)]):
+        a = gen.bernoulli_u8(m, n, 0.8, seed=9300 + 10 * w + k)
+        s = min(m, n, 20 + 3 * k)
+        a[m // 3:m // 3 + s, n - s:n] = 1
+        (K, r, c), _ = oracle.dp(a, want_map=False)
+        ld = (n + 15) // 16 * 16
+        big = torch.zeros((m, ld), dtype=torch.uint8, device=DEV)
+        big[:, :n] = to_dev(a)
+        mats.append(big[:, :n])
+        exps.append([K, r, c, 0])
+        mats.append((bits_dev(a, n, pad=1), n))
+        exps.append([K, r, c, 0])
+    assert ctx.batch(mats).cpu().tolist() == exps
+    for item, exp in zip(mats, exps):
+        one = ctx.batch([item, item]).cpu().tolist()
+        assert one == [exp, exp]
+
+
 def test_invalid_arguments(ctx, ms):
     x = torch.zeros((10, 10), dtype=torch.uint8, device=DEV)
     desc = ms.describe(x)
