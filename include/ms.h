@@ -26,7 +26,9 @@
  * - An empty matrix (m == 0 or n == 0) yields side 0 and row = col = -1, as
  *   Algorithm 1 returns 0 for an empty input (Sec. 3.2).
  * - No C++ exception crosses this interface.  A context is not thread-safe:
- *   use one per host thread (contexts may share a device).
+ *   use one per host thread (contexts may share a device).  Calls on one
+ *   context share its device workspace: issue them on one stream, or order
+ *   them, rather than on streams that run at the same time.
  * - Size limits: m <= 65000 rows and min(m, n) <= 32768; larger inputs
  *   return MS_ERR_UNSUPPORTED.  n itself is limited by m*n < 2^40 and
  *   n < 2^31 - 4096.
@@ -115,10 +117,13 @@ ms_status ms_all_max_squares(ms_ctx* ctx, const ms_matrix* in, int32_t* corners_
  * formats in one pass: the descriptors are read from HOST memory (ins_host),
  * the results go to outs_dev[0..count-1] in device memory.  Work from all
  * matrices is scheduled together: by default matrices up to about 900 000
- * cells are solved whole, one per block, in two persistent launches (their
- * bitplanes in shared memory), and larger ones as bitplane tiles of one
- * persistent launch followed by the exact fix-up of their flagged boxes
- * (see ms_tuning.tile_kind).  After a first call with a given set of
+ * cells are solved whole, one per block, in a persistent launch per size
+ * class (five classes; their bitplanes in shared memory), and larger ones as
+ * bitplane tiles of one persistent launch followed by the exact fix-up of
+ * their flagged boxes (see ms_tuning.tile_kind).  The size classes run on
+ * streams of the context's own, forked from `s` and joined back into it
+ * before the call returns, so all of the call's work stays ordered on `s`
+ * for the caller.  After a first call with a given set of
  * shapes, the same call (same pointers, shapes and count) may be captured in
  * a CUDA graph: it then allocates nothing and performs no host-device copy
  * other than stream-ordered ones issued inside the call. */
