@@ -306,7 +306,8 @@ ms_status ms_get_tuning(ms_ctx* ctx, ms_tuning* t);
  * count).  Later calls of that class with ms_tuning.band_rows == 0 and
  * lane_cols == 0 use the cached choice.  `outs_dev` receives results (count entries) and is
  * scratch.  Blocks the calling thread until the timing runs finish; must
- * not be called during stream capture.  The chosen tuning is written to
+ * not be called during stream capture, nor between ms_profile_start and
+ * ms_profile_stop (the profile would time the candidates' launches too).  The chosen tuning is written to
  * `chosen` if non-null. */
 ms_status ms_autotune(ms_ctx* ctx, const ms_matrix* ins_host, int32_t count, ms_result* outs_dev,
                       ms_stream_t s, ms_tuning* chosen);
